@@ -1,0 +1,323 @@
+#!/usr/bin/env python
+"""Benchmark: DOF-updates/s per RK stage of the quadrature-free DG shallow
+water solver (arXiv:1904.08684) on one GB300, through the libdgswe C-ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--impl ours|reference] [--no-cpu-baseline]
+
+Default workload: waves-p2-512 (512 x 512 quads -> 524,288 triangles, p = 2,
+periodic, h_b = 10 + 2 sin(2 pi x) cos(2 pi y), 8 seeded Gaussians, q = 0,
+SSP-RK3, CFL 0.2, FP64).  A step is one SSP-RK3 time step (3 stage-kernel
+launches, CUDA-graph captured); the metric counts 3 K E updated coefficients
+per stage.  The inputs are synthetic (seeded), projected on the device by the
+library's own set-up projection.
+
+N > 1 (torchrun): every rank runs an independent replica of the workload
+(the single-instance path has no domain decomposition); value = all ranks'
+DOF-updates / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the test reference) on the host
+cores, on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1904_08684_gb300 import inputs as I  # noqa: E402
+
+METRIC = "DOF-updates/s per RK stage"
+UNIT = "DOF/s"
+WORKLOADS = {
+    "waves-p2-512": lambda: I.waves_p2_512(),
+    "hump-p1-32": lambda: I.hump_p1_32(),
+    "hump-p3-32": lambda: I.hump_p3_32(),
+    "waves-p4-2048": lambda: I.waves_p4_2048(),
+    "waves-p2-512-fp32": lambda: I.waves_p2_512(precision="fp32"),
+    "waves-p3-512-fp32": lambda: I.waves_p2_512(p=3, precision="fp32"),
+}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP64 FMA rate of GB300 from the profiling recipe's nominal table; the
+# measured copy bandwidth comes from MEASURED_PEAKS.json
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max clock
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons (200 ms)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _setup_device_inputs(B, torch, wl, cfg, stream):
+    """seeded fields sampled at the library's set-up nodes, projected on the
+    device (dg_proj_nodes + dg_project)"""
+    E, K, Q = wl.E, wl.K, B.dg_proj_num_nodes(wl.p)
+    coef = []
+    chunk_fields = (wl.hb, wl.xi0)
+    xy = torch.empty((2, Q, E), dtype=torch.float64, device="cuda")
+    B.dg_proj_nodes(cfg, xy, stream)
+    torch.cuda.synchronize()
+    for f in chunk_fields:
+        vals = f(xy[0], xy[1]).contiguous()
+        c = torch.empty((K, E), dtype=torch.float64, device="cuda")
+        B.dg_project(cfg, vals, c, stream)
+        torch.cuda.synchronize()
+        coef.append(c)
+        del vals
+    del xy
+    zero = torch.zeros((K, E), dtype=torch.float64, device="cuda")
+    return coef[0], coef[1], zero, zero
+
+
+def run_ours(args):
+    import torch
+    from paper_1904_08684_gb300 import binding as B
+    from paper_1904_08684_gb300 import flops as FL
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.load()
+    wl = WORKLOADS[args.workload]()
+    cfg = B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc, precision=wl.precision, rk_order=wl.rk_order,
+                        cfl=wl.cfl, dt=wl.dt, g=wl.g, x0=wl.x0, y0=wl.y0, Lx=wl.Lx, Ly=wl.Ly,
+                        proj_precision=args.proj, block_size=args.block)
+    stream = torch.cuda.current_stream()
+    hb, xi, qx, qy = _setup_device_inputs(B, torch, wl, cfg, stream)
+    ctx = B.dg_init_device(cfg, hb, xi, qx, qy, stream)
+    del hb, xi, qx, qy
+    S = wl.rk_order
+    dof_stage = wl.dofs()
+    try:
+        B.dg_run(ctx, args.warmup)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            B.dg_run(ctx, args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        mass, energy = B.dg_diagnostics(ctx)
+        # end-to-end through the public API with host buffers: per step the
+        # state goes host -> device (dg_set_state), one dg_run step, and the
+        # state comes back (dg_get_state)
+        E, K = wl.E, wl.K
+        st = B.dg_get_state(ctx, E, K)
+        host = [torch.from_numpy(a).pin_memory().numpy() for a in st]
+        n_e2e = max(1, min(args.steps, args.e2e_steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            B.dg_set_state(ctx, *host, t=0.0)
+            B.dg_run(ctx, 1)
+            host = B.dg_get_state(ctx, E, K)
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+    finally:
+        B.dg_destroy(ctx)
+    step_ms = ms / args.steps
+    value = world * dof_stage * S / (step_ms * 1e-3)
+    # roofline of the stage kernel (the only kernel of the timed graphs)
+    launch_s = step_ms * 1e-3 / S
+    fp64 = wl.precision == "fp64"
+    word = 8 if fp64 else 4
+    flop = FL.stage_flops(wl.p) * wl.E
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    alg_bytes = FL.stage_bytes(wl.p, word) * wl.E
+    roof = {"bound": "alu", "achieved": flop / launch_s / 1e12,
+            "peak": FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "traffic": None,
+            "peak_source": ("FP64 1.25 TFLOP/s nominal (recipe table)" if fp64 else
+                            "FP32 152 SM x 128 lanes x 2 x 2.07 GHz"),
+            "hbm_achieved_gbs": alg_bytes / launch_s / 1e9,
+            "hbm_frac_of_measured": (alg_bytes / launch_s / 1e9) / hbm_peak if hbm_peak else None}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    e2e_val = dof_stage * S / e2e_s
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64" if fp64 else ("f32+f64solve" if args.proj == "fp64" else "f32"),
+           "data": "synthetic (seeded SplitMix64 fields, projected on device)",
+           "config": {"workload": wl.name, "elements": wl.E, "p": wl.p, "K": wl.K, "rk_stages": S,
+                      "dof_per_stage": dof_stage, "precision": wl.precision, "bc": wl.bc,
+                      "l2": "working set per stage > L2 (no flush)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "gpu_launches": S * args.steps,
+           "roofline": roof,
+           "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * wl.K * wl.E * 8,
+                   "d2h_bytes_per_step": 3 * wl.K * wl.E * 8},
+           "clocks": clk.summary(),
+           "diagnostics": {"mass": mass, "energy": energy}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline(wl, seconds):
+    """The FP64 oracle, as it stands, on the host cores: right-hand sides of a
+    contiguous block of elements (1/16 of the mesh) of the same workload,
+    repeated for about ``seconds``; one RHS evaluation is one RK stage."""
+    import oracle
+    o = oracle.Oracle(wl.nx, wl.ny, wl.p, bc=wl.bc, rk_order=wl.rk_order, cfl=wl.cfl, Lx=wl.Lx, Ly=wl.Ly)
+    nsamp = max(1, o.E // 16)
+    elems = np.arange(nsamp, dtype=np.int32)
+    # fields only where the sample and its neighbours need them
+    _, _, nb = o.geometry()
+    need = np.zeros(o.E, bool)
+    need[elems] = True
+    need[nb[elems][nb[elems] >= 0]] = True
+    xy = o.proj_nodes()
+    vals_hb = np.zeros(xy.shape[:2])
+    vals_xi = np.zeros(xy.shape[:2])
+    vals_hb[need] = wl.hb(xy[need][..., 0], xy[need][..., 1])
+    vals_xi[need] = wl.xi0(xy[need][..., 0], xy[need][..., 1])
+    hb = o.project_hb_values(vals_hb)
+    xi = o.project_values(vals_xi)
+    z = np.zeros_like(xi)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.rhs(hb, xi, z, z, elems=elems)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    rate = 3 * wl.K * nsamp * reps / el
+    return {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle RHS (one RK stage) of elements 0..%d of %s, %d repetitions, %.1f s"
+                      % (nsamp - 1, wl.name, reps, el)}
+
+
+def run_reference(args):
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]()
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_baseline(wl, per_step)
+    t0 = time.perf_counter()
+    rates = [cpu_baseline(wl, per_step) for _ in range(args.steps)]
+    el = time.perf_counter() - t0
+    value = statistics.mean(r["value"] for r in rates)
+    cb = dict(rates[-1])
+    cb["value"] = value
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded SplitMix64 fields)",
+           "config": {"workload": wl.name, "elements": wl.E, "p": wl.p, "K": wl.K,
+                      "rk_stages": wl.rk_order, "precision": "fp64", "bc": wl.bc},
+           "cpu_baseline": cb,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="waves-p2-512", choices=sorted(WORKLOADS))
+    ap.add_argument("--proj", default="fp64", choices=["fp64", "fp32"],
+                    help="velocity-solve arithmetic of the FP32 state path")
+    ap.add_argument("--block", type=int, default=0, help="threads per block (0 = library default)")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)      # timing rule: at least 3 untimed steps
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,160 @@
+/*
+ * dgswe.h -- C-ABI of libdgswe, a GB300 (sm_103a) implementation of the
+ * explicit right-hand side and Runge-Kutta stage update of the
+ * quadrature-free discontinuous Galerkin scheme for the 2D shallow water
+ * equations of Hajduk, Kuckuk et al., arXiv:1904.08684.
+ *
+ * Method (paper §2.1-2.2):
+ *   unknowns c = (xi, U, V) (surface elevation, discharge q = (U, V)), with
+ *   total depth H = xi + h_b; the velocity u = q/H is a second DG field
+ *   obtained element by element from (u H, psi) = (q, psi)  (Eq. (12));
+ *   the flux A~ of Eq. (8) is then polynomial, so every integral of the weak
+ *   form Eq. (11) is evaluated exactly from precomputed reference tensors;
+ *   the numerical flux is Lax-Friedrichs with one wave speed per edge,
+ *   lambda = max over both sides and the points s = 0, 1/2, 1 of
+ *   |u.n| + sqrt(g H).
+ * Mesh (paper §2.3): nx x ny quads over [x0, x0+Lx] x [y0, y0+Ly], each split
+ *   into two triangles along the diagonal from vertex (i+1, j) to (i, j+1);
+ *   element e = 2 (j nx + i) + t, t = 0 lower triangle (v_ij, v_i+1j,
+ *   v_ij+1), t = 1 upper triangle (v_i+1j+1, v_ij+1, v_i+1j), both
+ *   counter-clockwise so det B_e > 0.
+ * Basis (paper §2.2): on element e, phi_ei = phi^_i o F_e^-1 with the
+ *   orthonormal reference functions printed in §2.2 (K = 3, 6, 10 for
+ *   p = 1, 2, 3); p = 4 continues them by Gram-Schmidt of x^4, x^3 y,
+ *   x^2 y^2, x y^3, y^4 (K = 15).  The mass matrix is |det B_e| I.
+ * Time stepping (not stated in the paper; §3.1 uses a fixed dt): SSP
+ *   Runge-Kutta of order 1, 2 or 3 in Shu-Osher form; dt either fixed or
+ *   cfl * d_min / ((2p+1) max_e (|u_e| + sqrt(g H_e))) with element means and
+ *   d_min the smallest inscribed-circle diameter, evaluated on the device at
+ *   the start of every step.
+ *
+ * Conventions for every entry point:
+ *   - Host arrays are FP64, element-major ("AoS"): coefficient i of element e
+ *     at [e * K + i].  The caller owns them; the library copies what it needs.
+ *   - Device arrays are structure-of-arrays ("SoA"): field f, coefficient i,
+ *     element e at [(f * K + i) * E + e], in the context's precision (double
+ *     for DG_PREC_FP64, float for DG_PREC_FP32_MIXED).  The caller owns device
+ *     arrays it passes in; the library owns the buffers it allocates until
+ *     dg_destroy.
+ *   - All device work is ordered on the stream given to dg_init (NULL = the
+ *     legacy default stream).  Entry points that return host data
+ *     synchronise that stream.
+ *   - No C++ exception crosses this boundary; every failure is a dg_status.
+ *     After DG_ERR_DRY or DG_ERR_NONFINITE the context stays valid so the
+ *     state can be inspected; after DG_ERR_CUDA it should be destroyed.
+ */
+#ifndef DGSWE_H
+#define DGSWE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,         /* invalid argument (null pointer, size, value)    */
+  DG_ERR_UNSUPPORTED = 2, /* valid configuration this build does not provide */
+  DG_ERR_OOM = 3,         /* device allocation failed                        */
+  DG_ERR_CUDA = 4,        /* a CUDA runtime call failed                      */
+  DG_ERR_DRY = 5,         /* H <= 0 met: projection matrix not SPD or a
+                             wave-speed point with non-positive depth      */
+  DG_ERR_NONFINITE = 6,   /* a NaN or Inf appeared in the state              */
+  DG_ERR_TIMEOUT = 7      /* reserved: a bounded device wait gave up         */
+} dg_status;
+
+typedef enum { DG_BC_PERIODIC = 0, DG_BC_REFLECTIVE = 1, DG_BC_DIRICHLET = 2 } dg_bc;
+typedef enum { DG_PREC_FP64 = 0, DG_PREC_FP32_MIXED = 1 } dg_precision;
+typedef enum { DG_PROJ_FP64 = 0, DG_PROJ_FP32 = 1 } dg_proj_precision;
+
+typedef struct {
+  int nx, ny;              /* quads; E = 2 nx ny triangles                      */
+  double x0, y0, Lx, Ly;   /* domain                                            */
+  const double* vertex_xy; /* must be NULL: perturbed meshes are not built yet  */
+  int p;                   /* polynomial order, 1..4 (0 returns UNSUPPORTED)    */
+  double g;                /* gravitational acceleration                        */
+  int bc;                  /* dg_bc; DG_BC_DIRICHLET returns UNSUPPORTED        */
+  int precision;           /* dg_precision                                      */
+  int rk_order;            /* 1, 2 or 3 (SSP Runge-Kutta)                       */
+  double cfl;              /* used when dt <= 0                                 */
+  double dt;               /* > 0: fixed step                                   */
+  int proj_precision;      /* dg_proj_precision: arithmetic of the u = q/H
+                              solve in DG_PREC_FP32_MIXED (FP64 by default;
+                              DG_PREC_FP64 always solves in FP64)             */
+  int block_size;          /* threads per block of the stage kernels: 0 (=128),
+                              32, 64, 96 or 128                               */
+} dg_config;
+
+typedef struct dg_ctx dg_ctx;
+
+/* Number of basis functions K = (p+1)(p+2)/2 (0 for p outside 0..4). */
+int dg_num_basis(int p);
+
+/* Number of triangles 2 nx ny of a configuration (0 if invalid). */
+long long dg_num_elements(const dg_config* cfg);
+
+/* Create a context (paper §2.2 discrete unknowns c_ei, Eqs. (13)-(14)).
+ * hb: bathymetry coefficients, host FP64 AoS [E][K] (h_b is a DG field of the
+ * same order; the caller L2-projects it, see dg_project).  xi, qx, qy: the
+ * initial state, host FP64 AoS [E][K].  stream: a cudaStream_t or NULL.
+ * Allocates every device buffer the time loop needs; *out receives the
+ * context.  Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_init(const dg_config* cfg, const double* hb, const double* xi, const double* qx,
+                  const double* qy, void* stream, dg_ctx** out);
+
+/* As dg_init, but hb, xi, qx, qy are DEVICE arrays, FP64 SoA [K][E] (one
+ * field each), e.g. the output of dg_project.  They are copied. */
+dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_xi, const void* d_qx,
+                         const void* d_qy, void* stream, dg_ctx** out);
+
+/* Semi-discrete right-hand side (paper §2.2, Eq. (11) with the u-projection of
+ * Eq. (12)): d_rhs_out = M^-1 [ (A~, grad phi) - <A^, phi> + (r, phi) ] for
+ * the state d_state_in.  Both device SoA [3][K][E] (fields xi, U, V) in the
+ * context's precision; they must not overlap.  Uses the context's scratch
+ * buffers; does not change the context's own state.  Asynchronous. */
+dg_status dg_rhs(dg_ctx* ctx, const void* d_state_in, void* d_rhs_out);
+
+/* One SSP-RK step of the context's state.  If dt_used is not NULL the stream
+ * is synchronised and *dt_used receives the step's dt. */
+dg_status dg_rk_step(dg_ctx* ctx, double* dt_used);
+
+/* nsteps SSP-RK steps, each launched as one captured CUDA graph.  Synchronises
+ * the stream once at the end, reads the device error word and (if t_out is not
+ * NULL) the simulation time.  Returns DG_ERR_DRY / DG_ERR_NONFINITE if a
+ * kernel flagged one. */
+dg_status dg_run(dg_ctx* ctx, int nsteps, double* t_out);
+
+/* Copy the state to host FP64 AoS arrays [E][K] (each may be NULL). */
+dg_status dg_get_state(dg_ctx* ctx, double* xi, double* qx, double* qy);
+
+/* Replace the state (host FP64 AoS [E][K]) and the time. */
+dg_status dg_set_state(dg_ctx* ctx, const double* xi, const double* qx, const double* qy, double t);
+
+/* Device pointer of the context's state, SoA [3][K][E] in its precision. */
+dg_status dg_state_device(dg_ctx* ctx, void** d_state);
+
+/* mass = sum_e integral xi; energy = 1/2 sum_e integral (g xi^2 + U u + V v),
+ * both accumulated in FP64 in a fixed order (deterministic). */
+dg_status dg_diagnostics(dg_ctx* ctx, double* mass, double* energy);
+
+/* Set-up projection (not on the time-stepping path): nodes of the library's
+ * Gauss rule on every element, so that a caller can sample any function there
+ * and L2-project it.  dg_proj_num_nodes gives Q; dg_proj_nodes writes device
+ * FP64 [2][Q][E] (x then y); dg_project turns device FP64 samples [Q][E] into
+ * device FP64 SoA coefficients [K][E].  Asynchronous on stream. */
+int dg_proj_num_nodes(int p);
+dg_status dg_proj_nodes(const dg_config* cfg, void* d_xy, void* stream);
+dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, void* stream);
+
+/* Release every resource of the context (NULL is ignored). */
+void dg_destroy(dg_ctx* ctx);
+
+/* Static string naming a status. */
+const char* dg_status_str(dg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DGSWE_H */

@@ -175,6 +175,22 @@ class Oracle:
             raise RuntimeError("oracle projection failed")
         return coef
 
+    def project_values(self, vals):
+        """L2 projection onto P^p of values given at proj_nodes(), shape (E, Q)."""
+        vals = _f64(vals)
+        coef = np.zeros((self.E, self.K))
+        if self.lib.or_project(self._h, _ptr(vals), _ptr(coef)):
+            raise RuntimeError("oracle projection failed")
+        return coef
+
+    def project_hb_values(self, vals):
+        """as project_values, onto the bathymetry space P^max(p,1)"""
+        vals = _f64(vals)
+        coef = np.zeros((self.E, self.Kb))
+        if self.lib.or_project_hb(self._h, _ptr(vals), _ptr(coef)):
+            raise RuntimeError("oracle projection failed")
+        return coef
+
     def project_hb(self, f):
         """L2 projection of the bathymetry f(x, y) onto P^max(p,1)."""
         xy = self.proj_nodes()

@@ -1,0 +1,225 @@
+"""Thin ctypes binding of libdgswe (include/dgswe.h): same names, argument
+marshalling only.  Every computation runs in the library's CUDA kernels; if
+the library is missing this module raises instead of falling back.
+
+Host arrays are numpy float64, element-major (E, K).  Device arrays are
+torch CUDA tensors (or raw integer device pointers) in the library's SoA
+layout: state (3, K, E), single fields (K, E).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DG_OK, DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_DRY, DG_ERR_NONFINITE, DG_ERR_TIMEOUT = range(8)
+DG_BC_PERIODIC, DG_BC_REFLECTIVE, DG_BC_DIRICHLET = 0, 1, 2
+DG_PREC_FP64, DG_PREC_FP32_MIXED = 0, 1
+DG_PROJ_FP64, DG_PROJ_FP32 = 0, 1
+
+BC = {"periodic": DG_BC_PERIODIC, "reflective": DG_BC_REFLECTIVE, "dirichlet": DG_BC_DIRICHLET}
+PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
+
+# every entry point declared in include/dgswe.h
+EXPORTS = ["dg_num_basis", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
+           "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
+           "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str"]
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s" % (where, _status_name(status)))
+
+
+class dg_config(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+                ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+                ("vertex_xy", ctypes.POINTER(ctypes.c_double)),
+                ("p", ctypes.c_int), ("g", ctypes.c_double),
+                ("bc", ctypes.c_int), ("precision", ctypes.c_int), ("rk_order", ctypes.c_int),
+                ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
+                ("proj_precision", ctypes.c_int), ("block_size", ctypes.c_int)]
+
+
+def make_config(nx, ny, p, bc="periodic", precision="fp64", rk_order=3, cfl=0.2, dt=0.0, g=9.81,
+                x0=0.0, y0=0.0, Lx=1.0, Ly=1.0, proj_precision="fp64", block_size=0):
+    return dg_config(nx, ny, x0, y0, Lx, Ly, None, p, g,
+                     BC[bc] if isinstance(bc, str) else int(bc),
+                     PREC[precision] if isinstance(precision, str) else int(precision),
+                     rk_order, cfl, dt,
+                     DG_PROJ_FP32 if proj_precision == "fp32" else DG_PROJ_FP64, block_size)
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing=True):
+    """Load libdgswe.so (building it first if asked and needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build_library()
+    if not os.path.exists(path):
+        raise RuntimeError("libdgswe.so is not built (%s); run paper_1904_08684_gb300.build" % path)
+    lib = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    cp = ctypes.POINTER(dg_config)
+    lib.dg_num_basis.argtypes = [ctypes.c_int]
+    lib.dg_num_elements.argtypes = [cp]
+    lib.dg_num_elements.restype = ctypes.c_longlong
+    lib.dg_init.argtypes = [cp, dp, dp, dp, dp, vp, ctypes.POINTER(vp)]
+    lib.dg_init_device.argtypes = [cp, vp, vp, vp, vp, vp, ctypes.POINTER(vp)]
+    lib.dg_rhs.argtypes = [vp, vp, vp]
+    lib.dg_rk_step.argtypes = [vp, dp]
+    lib.dg_run.argtypes = [vp, ctypes.c_int, dp]
+    lib.dg_get_state.argtypes = [vp, dp, dp, dp]
+    lib.dg_set_state.argtypes = [vp, dp, dp, dp, ctypes.c_double]
+    lib.dg_state_device.argtypes = [vp, ctypes.POINTER(vp)]
+    lib.dg_diagnostics.argtypes = [vp, dp, dp]
+    lib.dg_proj_num_nodes.argtypes = [ctypes.c_int]
+    lib.dg_proj_nodes.argtypes = [cp, vp, vp]
+    lib.dg_project.argtypes = [cp, vp, vp, vp]
+    lib.dg_destroy.argtypes = [vp]
+    lib.dg_destroy.restype = None
+    lib.dg_status_str.argtypes = [ctypes.c_int]
+    lib.dg_status_str.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _status_name(s):
+    try:
+        return load(False).dg_status_str(s).decode()
+    except Exception:  # library not loadable: numeric code only
+        return "status %d" % s
+
+
+def _check(s, where):
+    if s != DG_OK:
+        raise DGError(s, where)
+
+
+def _dptr(x):
+    """device pointer of a torch tensor or an int"""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _hptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _host(a, E, K):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.size != E * K:
+        raise ValueError("expected %d x %d coefficients, got shape %s" % (E, K, a.shape))
+    return a
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---------------------------------------------------------------- entry points
+def dg_num_basis(p):
+    return load().dg_num_basis(int(p))
+
+
+def dg_num_elements(cfg):
+    return load().dg_num_elements(ctypes.byref(cfg))
+
+
+def dg_init(cfg, hb, xi, qx, qy, stream=None):
+    """Context from host FP64 (E, K) arrays; returns an opaque handle."""
+    lib = load()
+    E, K = dg_num_elements(cfg), dg_num_basis(cfg.p)
+    arrs = [_host(a, E, K) for a in (hb, xi, qx, qy)]
+    h = ctypes.c_void_p()
+    _check(lib.dg_init(ctypes.byref(cfg), *[_hptr(a) for a in arrs], _stream(stream), ctypes.byref(h)),
+           "dg_init")
+    return h
+
+
+def dg_init_device(cfg, d_hb, d_xi, d_qx, d_qy, stream=None):
+    """Context from device FP64 (K, E) arrays."""
+    lib = load()
+    h = ctypes.c_void_p()
+    _check(lib.dg_init_device(ctypes.byref(cfg), _dptr(d_hb), _dptr(d_xi), _dptr(d_qx), _dptr(d_qy),
+                              _stream(stream), ctypes.byref(h)), "dg_init_device")
+    return h
+
+
+def dg_rhs(ctx, d_state_in, d_rhs_out):
+    _check(load().dg_rhs(ctx, _dptr(d_state_in), _dptr(d_rhs_out)), "dg_rhs")
+
+
+def dg_rk_step(ctx, want_dt=False):
+    dt = ctypes.c_double(0.0)
+    _check(load().dg_rk_step(ctx, ctypes.byref(dt) if want_dt else None), "dg_rk_step")
+    return dt.value if want_dt else None
+
+
+def dg_run(ctx, nsteps):
+    t = ctypes.c_double(0.0)
+    _check(load().dg_run(ctx, int(nsteps), ctypes.byref(t)), "dg_run")
+    return t.value
+
+
+def dg_get_state(ctx, E, K):
+    out = [np.zeros((E, K)) for _ in range(3)]
+    _check(load().dg_get_state(ctx, *[_hptr(a) for a in out]), "dg_get_state")
+    return out
+
+
+def dg_set_state(ctx, xi, qx, qy, t=0.0):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (xi, qx, qy)]
+    _check(load().dg_set_state(ctx, *[_hptr(a) for a in arrs], float(t)), "dg_set_state")
+
+
+def dg_state_device(ctx):
+    p = ctypes.c_void_p()
+    _check(load().dg_state_device(ctx, ctypes.byref(p)), "dg_state_device")
+    return p.value
+
+
+def dg_diagnostics(ctx):
+    m, e = ctypes.c_double(), ctypes.c_double()
+    _check(load().dg_diagnostics(ctx, ctypes.byref(m), ctypes.byref(e)), "dg_diagnostics")
+    return m.value, e.value
+
+
+def dg_proj_num_nodes(p):
+    return load().dg_proj_num_nodes(int(p))
+
+
+def dg_proj_nodes(cfg, d_xy, stream=None):
+    _check(load().dg_proj_nodes(ctypes.byref(cfg), _dptr(d_xy), _stream(stream)), "dg_proj_nodes")
+
+
+def dg_project(cfg, d_vals, d_coef, stream=None):
+    _check(load().dg_project(ctypes.byref(cfg), _dptr(d_vals), _dptr(d_coef), _stream(stream)), "dg_project")
+
+
+def dg_destroy(ctx):
+    if ctx:
+        load().dg_destroy(ctx)
+
+
+def dg_status_str(s):
+    return load().dg_status_str(int(s)).decode()

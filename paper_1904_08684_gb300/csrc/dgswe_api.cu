@@ -1,0 +1,552 @@
+// dgswe_api.cu -- C-ABI of libdgswe (declared in include/dgswe.h): contexts,
+// device buffers, graph-captured time steps, set-up projection, diagnostics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dg_launch.cuh"
+#include "dgswe.h"
+
+using namespace dgswe;
+
+namespace {
+
+struct GraphSlot {
+  cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct dg_ctx {
+  dg_config cfg;
+  int P, K, K1, P1, NREC;
+  long long E;
+  int arith;
+  size_t rsz;  // bytes per Real
+  Mesh mesh;
+  double inv_det, det, cfl_num;
+  cudaStream_t stream;   // caller's stream
+  cudaStream_t cap;      // private stream used only for graph capture
+  // device buffers
+  void* w[3];            // state w0 (step start / result), w1, w2 (stage outputs)
+  void* vs[2];           // volume+source integrals of the evaluated state
+  void* rec[2];          // side records of the evaluated state
+  void* hb;              // [K][E]
+  void* hbt;             // [3][P1][E]
+  void* ghb;             // [2][K1][E]
+  double* scal;          // [0],[1]: wave-speed slots, [2]: t, [3]: last dt
+  unsigned* err;
+  double* partial;       // diagnostics partial sums
+  void* rhs_vs;          // scratch of dg_rhs
+  void* rhs_rec;
+  int ep;                // eval buffer holding the current state's evaluation
+  int lc;                // wave-speed slot of the current state
+  bool evaluated;
+  GraphSlot graph[2][2];
+};
+
+namespace {
+
+int K_of(int p) { return (p + 1) * (p + 2) / 2; }
+
+dg_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DG_OK;
+  if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+  return DG_ERR_CUDA;
+}
+
+#define CK(x)                                 \
+  do {                                        \
+    cudaError_t _e = (x);                     \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+dg_status validate(const dg_config* c) {
+  if (!c) return DG_ERR_ARG;
+  if (c->nx < 1 || c->ny < 1 || c->p < 0 || c->p > 4) return DG_ERR_ARG;
+  if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
+  if (c->rk_order < 1 || c->rk_order > 3) return DG_ERR_ARG;
+  if (c->bc < 0 || c->bc > 2 || c->precision < 0 || c->precision > 1) return DG_ERR_ARG;
+  if (c->proj_precision < 0 || c->proj_precision > 1) return DG_ERR_ARG;
+  if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
+  // the stage kernels are compiled for at most 128 threads per block
+  if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 128 || c->block_size % 32)) return DG_ERR_ARG;
+  if (c->bc == DG_BC_PERIODIC && (c->nx < 2 || c->ny < 2)) return DG_ERR_ARG;
+  if (c->p == 0 || c->bc == DG_BC_DIRICHLET || c->vertex_xy) return DG_ERR_UNSUPPORTED;
+  if (2.0 * (double)c->nx * (double)c->ny > 4.0e9) return DG_ERR_ARG;
+  return DG_OK;
+}
+
+cudaError_t launch_stage_any(const dg_ctx* c, int mode, const void* params, cudaStream_t s) {
+  const int block = c->cfg.block_size ? c->cfg.block_size : 128;
+  switch (c->arith) {
+    case ARITH_FP64: return stage_fp64(c->P, mode, block, params, s);
+    case ARITH_FP32_P64: return stage_fp32p64(c->P, mode, block, params, s);
+    default: return stage_fp32p32(c->P, mode, block, params, s);
+  }
+}
+
+template <class Real>
+StageParams<Real> base_params(const dg_ctx* c) {
+  StageParams<Real> sp;
+  std::memset(&sp, 0, sizeof sp);
+  sp.m = c->mesh;
+  sp.g = Real(c->cfg.g);
+  sp.hb = (const Real*)c->hb;
+  sp.hbt = (const Real*)c->hbt;
+  sp.ghb = (const Real*)c->ghb;
+  sp.dt_fixed = c->cfg.dt > 0.0 ? c->cfg.dt : 0.0;
+  sp.cfl_num = c->cfl_num;
+  sp.inv_det = c->inv_det;
+  sp.err = c->err;
+  return sp;
+}
+
+// Evaluation of the state in buffer w into (vs[ep], rec[ep]) and its wave
+// speed into slot lc.
+template <class Real>
+dg_status launch_eval_t(dg_ctx* c, cudaStream_t s) {
+  CK(cudaMemsetAsync(c->scal + c->lc, 0, sizeof(double), s));
+  StageParams<Real> sp = base_params<Real>(c);
+  sp.w = (const Real*)c->w[0];
+  sp.vs_out = (Real*)c->vs[c->ep];
+  sp.rec_out = (Real*)c->rec[c->ep];
+  sp.lam_next = c->scal + c->lc;
+  CK(launch_stage_any(c, MODE_EVAL, &sp, s));
+  return DG_OK;
+}
+
+// Shu-Osher coefficients of SSP-RK1/2/3: w_{s+1} = a_s w_0 + b_s (w_s + dt R(w_s))
+const double RK_A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.75, 1.0 / 3.0}};
+const double RK_B[3][3] = {{1.0, 0.0, 0.0}, {1.0, 0.5, 0.0}, {1.0, 0.25, 2.0 / 3.0}};
+
+// Launch one full time step from eval parity ep, wave-speed slot lc.
+template <class Real>
+dg_status launch_step_t(const dg_ctx* c, int ep, int lc, cudaStream_t s) {
+  const int S = c->cfg.rk_order;
+  const bool adaptive = !(c->cfg.dt > 0.0);
+  if (adaptive) CK(cudaMemsetAsync(c->scal + (1 - lc), 0, sizeof(double), s));
+  for (int st = 0; st < S; ++st) {
+    StageParams<Real> sp = base_params<Real>(c);
+    sp.w = (const Real*)(st == 0 ? c->w[0] : c->w[st]);
+    sp.wout = (Real*)(st == S - 1 ? c->w[0] : c->w[st + 1]);
+    sp.w0 = (const Real*)c->w[0];
+    sp.alpha = RK_A[S - 1][st];
+    sp.beta = RK_B[S - 1][st];
+    const int pin = (ep + st) & 1;
+    sp.vs = (const Real*)c->vs[pin];
+    sp.rec = (const Real*)c->rec[pin];
+    sp.vs_out = (Real*)c->vs[1 - pin];
+    sp.rec_out = (Real*)c->rec[1 - pin];
+    sp.lam = c->scal + lc;
+    if (st == S - 1) {
+      if (adaptive) sp.lam_next = c->scal + (1 - lc);
+      sp.t = c->scal + 2;
+    }
+    CK(launch_stage_any(c, MODE_STAGE, &sp, s));
+  }
+  return DG_OK;
+}
+
+dg_status launch_step(const dg_ctx* c, int ep, int lc, cudaStream_t s) {
+  return c->arith == ARITH_FP64 ? launch_step_t<double>(c, ep, lc, s) : launch_step_t<float>(c, ep, lc, s);
+}
+
+dg_status launch_eval(dg_ctx* c, cudaStream_t s) {
+  return c->arith == ARITH_FP64 ? launch_eval_t<double>(c, s) : launch_eval_t<float>(c, s);
+}
+
+dg_status ensure_evaluated(dg_ctx* c) {
+  if (c->evaluated) return DG_OK;
+  dg_status st = launch_eval(c, c->stream);
+  if (st != DG_OK) return st;
+  c->evaluated = true;
+  return DG_OK;
+}
+
+dg_status get_graph(dg_ctx* c, cudaGraphExec_t* out) {
+  GraphSlot& g = c->graph[c->ep][c->lc];
+  if (!g.exec) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    dg_status st = launch_step(c, c->ep, c->lc, c->cap);
+    cudaError_t ce = cudaStreamEndCapture(c->cap, &graph);
+    if (st != DG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    CK(ce);
+    ce = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ce);
+  }
+  *out = g.exec;
+  return DG_OK;
+}
+
+void advance_parity(dg_ctx* c) {
+  c->ep = (c->ep + c->cfg.rk_order) & 1;
+  if (!(c->cfg.dt > 0.0)) c->lc = 1 - c->lc;
+}
+
+dg_status read_err(dg_ctx* c) {
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(&h, c->err, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (h) {
+    // report once: clear the word so the context can be inspected and reused
+    CK(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  if (h & ERRF_NONFINITE) return DG_ERR_NONFINITE;
+  if (h & ERRF_DRY) return DG_ERR_DRY;
+  return DG_OK;
+}
+
+// host AoS FP64 [E][K] -> device SoA FP64 [K][E] (staging through a pinned
+// or pageable host transpose)
+dg_status upload_soa(const double* host, long long E, int K, double* dev, cudaStream_t s) {
+  std::vector<double> t((size_t)E * K);
+  for (long long e = 0; e < E; ++e)
+    for (int i = 0; i < K; ++i) t[(size_t)i * E + e] = host[(size_t)e * K + i];
+  CK(cudaMemcpyAsync(dev, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+__global__ void cvt_kernel_f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = float(a[i]);
+}
+__global__ void cvt_kernel_b(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = double(a[i]);
+}
+
+// device FP64 -> context precision
+dg_status store_real(const dg_ctx* c, const double* src, void* dst, long long n, cudaStream_t s) {
+  if (c->arith == ARITH_FP64) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else if (n > 0) {
+    cvt_kernel_f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (float*)dst, n);
+    CK(cudaGetLastError());
+  }
+  return DG_OK;
+}
+dg_status load_real(const dg_ctx* c, const void* src, double* dst, long long n, cudaStream_t s) {
+  if (c->arith == ARITH_FP64) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else if (n > 0) {
+    cvt_kernel_b<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, dst, n);
+    CK(cudaGetLastError());
+  }
+  return DG_OK;
+}
+
+void free_ctx(dg_ctx* c) {
+  if (!c) return;
+  for (auto& row : c->graph)
+    for (auto& g : row)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+  void* bufs[] = {c->w[0], c->w[1], c->w[2], c->vs[0], c->vs[1], c->rec[0], c->rec[1], c->hb, c->hbt,
+                  c->ghb, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+// Common part of dg_init / dg_init_device: d_fields = device FP64 SoA
+// [4][K][E] (hb, xi, qx, qy), owned by the caller of this helper.
+dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, const double* d_qx,
+                 const double* d_qy, void* stream, dg_ctx** out) {
+  dg_ctx* c = new (std::nothrow) dg_ctx;
+  if (!c) return DG_ERR_OOM;
+  std::memset(c, 0, sizeof *c);
+  c->cfg = *cfg;
+  c->P = cfg->p;
+  c->K = K_of(cfg->p);
+  c->K1 = K_of(cfg->p - 1);
+  c->P1 = cfg->p + 1;
+  c->NREC = 6 * c->P1 + 1;
+  c->E = 2LL * cfg->nx * cfg->ny;
+  c->arith = cfg->precision == DG_PREC_FP64 ? ARITH_FP64
+                                            : (cfg->proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32 : ARITH_FP32_P64);
+  c->rsz = c->arith == ARITH_FP64 ? sizeof(double) : sizeof(float);
+  c->stream = (cudaStream_t)stream;
+  const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
+  c->mesh.nx = cfg->nx;
+  c->mesh.ny = cfg->ny;
+  c->mesh.E = c->E;
+  c->mesh.hx = hx;
+  c->mesh.hy = hy;
+  c->mesh.diag = std::hypot(hx, hy);
+  c->mesh.periodic = cfg->bc == DG_BC_PERIODIC;
+  c->det = hx * hy;
+  c->inv_det = 1.0 / c->det;
+  // smallest inscribed-circle diameter 4 area / perimeter (all triangles equal)
+  const double dmin = 4.0 * (0.5 * c->det) / (hx + hy + std::hypot(hx, hy));
+  c->cfl_num = cfg->cfl * dmin / (2.0 * cfg->p + 1.0);
+  const long long E = c->E;
+  const size_t st = (size_t)3 * c->K * E * c->rsz;
+  dg_status s = DG_OK;
+  auto alloc = [&](void** p, size_t n) {
+    if (s != DG_OK) return;
+    cudaError_t e = cudaMalloc(p, n);
+    if (e != cudaSuccess) s = cuda_status(e);
+  };
+  for (int i = 0; i < 3; ++i) alloc(&c->w[i], st);
+  for (int i = 0; i < 2; ++i) {
+    alloc(&c->vs[i], st);
+    alloc(&c->rec[i], (size_t)3 * c->NREC * E * c->rsz);
+  }
+  alloc(&c->hb, (size_t)c->K * E * c->rsz);
+  alloc(&c->hbt, (size_t)3 * c->P1 * E * c->rsz);
+  alloc(&c->ghb, (size_t)2 * c->K1 * E * c->rsz);
+  alloc((void**)&c->scal, 4 * sizeof(double));
+  alloc((void**)&c->err, sizeof(unsigned));
+  alloc((void**)&c->partial, sizeof(double) * 2 * (size_t)((E + 127) / 128));
+  if (s == DG_OK) {
+    cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) s = cuda_status(e);
+  }
+  if (s != DG_OK) {
+    free_ctx(c);
+    return s;
+  }
+  cudaStream_t ss = c->stream;
+  cudaError_t ce = cudaMemsetAsync(c->scal, 0, 4 * sizeof(double), ss);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(c->err, 0, sizeof(unsigned), ss);
+  if (ce != cudaSuccess) {
+    free_ctx(c);
+    return cuda_status(ce);
+  }
+  const long long KE = (long long)c->K * E;
+  char* w0 = (char*)c->w[0];
+  if ((s = store_real(c, d_xi, w0, KE, ss)) != DG_OK || (s = store_real(c, d_qx, w0 + KE * c->rsz, KE, ss)) != DG_OK ||
+      (s = store_real(c, d_qy, w0 + 2 * KE * c->rsz, KE, ss)) != DG_OK) {
+    free_ctx(c);
+    return s;
+  }
+  cudaError_t le;
+  switch (c->arith) {
+    case ARITH_FP64: le = static_fp64(c->P, c->mesh, d_hb, c->hb, c->hbt, c->ghb, ss); break;
+    case ARITH_FP32_P64: le = static_fp32p64(c->P, c->mesh, d_hb, c->hb, c->hbt, c->ghb, ss); break;
+    default: le = static_fp32p32(c->P, c->mesh, d_hb, c->hb, c->hbt, c->ghb, ss); break;
+  }
+  if (le == cudaSuccess) le = cudaStreamSynchronize(ss);
+  if (le != cudaSuccess) {
+    free_ctx(c);
+    return cuda_status(le);
+  }
+  *out = c;
+  return DG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+int dg_num_basis(int p) { return (p < 0 || p > 4) ? 0 : K_of(p); }
+
+long long dg_num_elements(const dg_config* cfg) {
+  if (!cfg || cfg->nx < 1 || cfg->ny < 1) return 0;
+  return 2LL * cfg->nx * cfg->ny;
+}
+
+const char* dg_status_str(dg_status s) {
+  switch (s) {
+    case DG_OK: return "DG_OK";
+    case DG_ERR_ARG: return "DG_ERR_ARG";
+    case DG_ERR_UNSUPPORTED: return "DG_ERR_UNSUPPORTED";
+    case DG_ERR_OOM: return "DG_ERR_OOM";
+    case DG_ERR_CUDA: return "DG_ERR_CUDA";
+    case DG_ERR_DRY: return "DG_ERR_DRY";
+    case DG_ERR_NONFINITE: return "DG_ERR_NONFINITE";
+    case DG_ERR_TIMEOUT: return "DG_ERR_TIMEOUT";
+  }
+  return "DG_ERR_UNKNOWN";
+}
+
+dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_xi, const void* d_qx,
+                         const void* d_qy, void* stream, dg_ctx** out) {
+  dg_status s = validate(cfg);
+  if (s != DG_OK) return s;
+  if (!d_hb || !d_xi || !d_qx || !d_qy || !out) return DG_ERR_ARG;
+  return create(cfg, (const double*)d_hb, (const double*)d_xi, (const double*)d_qx, (const double*)d_qy, stream,
+                out);
+}
+
+dg_status dg_init(const dg_config* cfg, const double* hb, const double* xi, const double* qx, const double* qy,
+                  void* stream, dg_ctx** out) {
+  dg_status s = validate(cfg);
+  if (s != DG_OK) return s;
+  if (!hb || !xi || !qx || !qy || !out) return DG_ERR_ARG;
+  const int K = K_of(cfg->p);
+  const long long E = 2LL * cfg->nx * cfg->ny;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMalloc(&tmp, sizeof(double) * 4 * (size_t)K * E);
+  if (e != cudaSuccess) return cuda_status(e);
+  cudaStream_t ss = (cudaStream_t)stream;
+  const double* src[4] = {hb, xi, qx, qy};
+  for (int f = 0; f < 4 && s == DG_OK; ++f) s = upload_soa(src[f], E, K, tmp + (size_t)f * K * E, ss);
+  if (s == DG_OK)
+    s = create(cfg, tmp, tmp + (size_t)K * E, tmp + 2 * (size_t)K * E, tmp + 3 * (size_t)K * E, stream, out);
+  cudaStreamSynchronize(ss);
+  cudaFree(tmp);
+  return s;
+}
+
+void dg_destroy(dg_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+}
+
+dg_status dg_rhs(dg_ctx* c, const void* d_in, void* d_out) {
+  if (!c || !d_in || !d_out || d_in == d_out) return DG_ERR_ARG;
+  const long long E = c->E;
+  if (!c->rhs_vs) {
+    CK(cudaMalloc(&c->rhs_vs, (size_t)3 * c->K * E * c->rsz));
+    CK(cudaMalloc(&c->rhs_rec, (size_t)3 * c->NREC * E * c->rsz));
+  }
+  if (c->arith == ARITH_FP64) {
+    StageParams<double> sp = base_params<double>(c);
+    sp.w = (const double*)d_in;
+    sp.vs_out = (double*)c->rhs_vs;
+    sp.rec_out = (double*)c->rhs_rec;
+    CK(launch_stage_any(c, MODE_EVAL, &sp, c->stream));
+    sp.vs = (const double*)c->rhs_vs;
+    sp.rec = (const double*)c->rhs_rec;
+    sp.rhs_out = (double*)d_out;
+    CK(launch_stage_any(c, MODE_RHS, &sp, c->stream));
+  } else {
+    StageParams<float> sp = base_params<float>(c);
+    sp.w = (const float*)d_in;
+    sp.vs_out = (float*)c->rhs_vs;
+    sp.rec_out = (float*)c->rhs_rec;
+    CK(launch_stage_any(c, MODE_EVAL, &sp, c->stream));
+    sp.vs = (const float*)c->rhs_vs;
+    sp.rec = (const float*)c->rhs_rec;
+    sp.rhs_out = (float*)d_out;
+    CK(launch_stage_any(c, MODE_RHS, &sp, c->stream));
+  }
+  return DG_OK;
+}
+
+dg_status dg_run(dg_ctx* c, int nsteps, double* t_out) {
+  if (!c || nsteps < 0) return DG_ERR_ARG;
+  dg_status s = ensure_evaluated(c);
+  if (s != DG_OK) return s;
+  for (int k = 0; k < nsteps; ++k) {
+    cudaGraphExec_t g;
+    if ((s = get_graph(c, &g)) != DG_OK) return s;
+    CK(cudaGraphLaunch(g, c->stream));
+    advance_parity(c);
+  }
+  if ((s = read_err(c)) != DG_OK) return s;
+  if (t_out) {
+    CK(cudaMemcpyAsync(t_out, c->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  return DG_OK;
+}
+
+dg_status dg_rk_step(dg_ctx* c, double* dt_used) {
+  if (!c) return DG_ERR_ARG;
+  dg_status s = ensure_evaluated(c);
+  if (s != DG_OK) return s;
+  double dt = c->cfg.dt;
+  if (dt_used && !(c->cfg.dt > 0.0)) {
+    double lam = 0.0;
+    CK(cudaMemcpyAsync(&lam, c->scal + c->lc, sizeof lam, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dt = c->cfl_num / lam;
+  }
+  if ((s = launch_step(c, c->ep, c->lc, c->stream)) != DG_OK) return s;
+  advance_parity(c);
+  if (dt_used) {
+    CK(cudaStreamSynchronize(c->stream));
+    *dt_used = dt;
+  }
+  return DG_OK;
+}
+
+dg_status dg_state_device(dg_ctx* c, void** d_state) {
+  if (!c || !d_state) return DG_ERR_ARG;
+  *d_state = c->w[0];
+  return DG_OK;
+}
+
+dg_status dg_get_state(dg_ctx* c, double* xi, double* qx, double* qy) {
+  if (!c) return DG_ERR_ARG;
+  const long long E = c->E, KE = (long long)c->K * E;
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * 3 * KE));
+  dg_status s = load_real(c, c->w[0], tmp, 3 * KE, c->stream);
+  std::vector<double> h((size_t)3 * KE);
+  cudaError_t e = cudaMemcpyAsync(h.data(), tmp, sizeof(double) * 3 * KE, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  if (s != DG_OK) return s;
+  CK(e);
+  double* dst[3] = {xi, qx, qy};
+  for (int f = 0; f < 3; ++f) {
+    if (!dst[f]) continue;
+    const double* src = h.data() + (size_t)f * KE;
+    for (long long el = 0; el < E; ++el)
+      for (int i = 0; i < c->K; ++i) dst[f][(size_t)el * c->K + i] = src[(size_t)i * E + el];
+  }
+  return DG_OK;
+}
+
+dg_status dg_set_state(dg_ctx* c, const double* xi, const double* qx, const double* qy, double t) {
+  if (!c || !xi || !qx || !qy) return DG_ERR_ARG;
+  const long long E = c->E, KE = (long long)c->K * E;
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * 3 * KE));
+  const double* src[3] = {xi, qx, qy};
+  dg_status s = DG_OK;
+  for (int f = 0; f < 3 && s == DG_OK; ++f) s = upload_soa(src[f], E, c->K, tmp + (size_t)f * KE, c->stream);
+  if (s == DG_OK) s = store_real(c, tmp, c->w[0], 3 * KE, c->stream);
+  cudaError_t e = cudaMemcpyAsync(c->scal + 2, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e2 = cudaStreamSynchronize(c->stream);
+  cudaFree(tmp);
+  if (s != DG_OK) return s;
+  CK(e);
+  CK(e2);
+  c->evaluated = false;
+  return DG_OK;
+}
+
+dg_status dg_diagnostics(dg_ctx* c, double* mass, double* energy) {
+  if (!c) return DG_ERR_ARG;
+  const long long nb = (c->E + 127) / 128;
+  cudaError_t e;
+  switch (c->arith) {
+    case ARITH_FP64: e = diag_fp64(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream); break;
+    case ARITH_FP32_P64:
+      e = diag_fp32p64(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream);
+      break;
+    default: e = diag_fp32p32(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream); break;
+  }
+  CK(e);
+  std::vector<double> h((size_t)2 * nb);
+  CK(cudaMemcpyAsync(h.data(), c->partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  double m = 0.0, en = 0.0;
+  for (long long b = 0; b < nb; ++b) {
+    m += h[2 * b];
+    en += h[2 * b + 1];
+  }
+  if (mass) *mass = m;
+  if (energy) *energy = en;
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -31,6 +31,15 @@ import numpy as np
 _MASK = (1 << 64) - 1
 
 
+def _xp(x):
+    """numpy, or torch when the coordinates are torch tensors (fields can then
+    be sampled directly on a GPU)"""
+    if type(x).__module__.startswith("torch"):
+        import torch
+        return torch
+    return np
+
+
 def splitmix64(seed: int, n: int) -> np.ndarray:
     """n outputs of Vigna's SplitMix64 generator started from ``seed``
     (output k mixes the counter seed + (k + 1) * 0x9E3779B97F4A7C15)."""
@@ -58,42 +67,43 @@ def uniform_int(seed: int, n: int, lo: int, hi: int) -> np.ndarray:
 # fields
 
 def gaussian_sum(amps, sigmas, cx, cy, periodic=True, L=1.0):
-    """xi_0 = sum_k A_k exp(-d_k^2 / (2 sigma_k^2)); with ``periodic`` d is the
-    distance to the nearest of the 3 x 3 periodic images of each centre."""
+    """xi_0 = sum_k A_k exp(-d_k^2 / (2 sigma_k^2)); with ``periodic`` the sum
+    runs over the 3 x 3 periodic images of each centre (separable in x, y)."""
     amps, sigmas, cx, cy = (np.asarray(a, dtype=np.float64) for a in (amps, sigmas, cx, cy))
 
     def f(x, y):
-        x = np.asarray(x, dtype=np.float64)
-        y = np.asarray(y, dtype=np.float64)
-        out = np.zeros(np.broadcast(x, y).shape)
+        xp = _xp(x)
+        out = 0.0 * x + 0.0 * y
         shifts = (-L, 0.0, L) if periodic else (0.0,)
         for A, s, ax, ay in zip(amps, sigmas, cx, cy):
-            for sx in shifts:
-                for sy in shifts:
-                    d2 = (x - ax - sx) ** 2 + (y - ay - sy) ** 2
-                    out += A * np.exp(-d2 / (2.0 * s * s))
+            c = -1.0 / (2.0 * s * s)
+            gx = sum(xp.exp(c * (x - ax - sx) ** 2) for sx in shifts)
+            gy = sum(xp.exp(c * (y - ay - sy) ** 2) for sy in shifts)
+            out = out + A * gx * gy
         return out
     return f
 
 
 def constant(c):
     def f(x, y):
-        return np.full(np.broadcast(np.asarray(x), np.asarray(y)).shape, float(c))
+        return 0.0 * x + 0.0 * y + float(c)
     return f
 
 
 def sin_cos_bathymetry(x, y):
     """h_b = 10 + 2 sin(2 pi x) cos(2 pi y)."""
-    return 10.0 + 2.0 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+    xp = _xp(x)
+    return 10.0 + 2.0 * xp.sin(2 * np.pi * x) * xp.cos(2 * np.pi * y)
 
 
 def fourier_bathymetry(mean, amps, ms, ns, kinds):
     """h_b = mean + sum_k a_k trig_k(2 pi (m_k x + n_k y)), trig = sin or cos."""
     def f(x, y):
-        out = np.full(np.broadcast(np.asarray(x), np.asarray(y)).shape, float(mean))
+        xp = _xp(x)
+        out = 0.0 * x + 0.0 * y + float(mean)
         for a, m, n, kd in zip(amps, ms, ns, kinds):
-            arg = 2 * np.pi * (m * np.asarray(x) + n * np.asarray(y))
-            out = out + a * (np.sin(arg) if kd == 0 else np.cos(arg))
+            arg = 2 * np.pi * (float(m) * x + float(n) * y)
+            out = out + float(a) * (xp.sin(arg) if kd == 0 else xp.cos(arg))
         return out
     return f
 
@@ -104,19 +114,19 @@ MS_CA, MS_CT, MS_YA = 0.2, 0.2, 0.3
 
 
 def ms_xi(x, y, t=0.0):
-    return 2.0 + MS_YA - 2.0 * MS_CA * np.sin(np.pi * (x + y + MS_CT * t) / 600.0)
+    return 2.0 + MS_YA - 2.0 * MS_CA * _xp(x).sin(np.pi * (x + y + MS_CT * t) / 600.0)
 
 
 def ms_U(x, y, t=0.0):
-    return 2.0 * MS_YA + MS_CA * MS_CT * np.sin(np.pi * (x + y + MS_CT * t) / 600.0)
+    return 2.0 * MS_YA + MS_CA * MS_CT * _xp(x).sin(np.pi * (x + y + MS_CT * t) / 600.0)
 
 
 def ms_V(x, y, t=0.0):
-    return MS_YA + MS_CA * MS_CT * np.sin(np.pi * (x + y + MS_CT * t) / 600.0)
+    return MS_YA + MS_CA * MS_CT * _xp(x).sin(np.pi * (x + y + MS_CT * t) / 600.0)
 
 
 def ms_hb(x, y):
-    return 1.0 + np.asarray(x) / 1000.0 + 2.0 * np.asarray(y) / 1000.0
+    return 1.0 + x / 1000.0 + 2.0 * y / 1000.0
 
 
 def perturbed_vertices(nx, ny, Lx, Ly, frac=0.2, seed=7, x0=0.0, y0=0.0):

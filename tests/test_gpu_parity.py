@@ -1,0 +1,284 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Every input is produced by the oracle's own L2 projection of the seeded
+workload fields and handed to both sides unchanged.  Tolerances:
+  * FP64 right-hand side: max |GPU - oracle| <= 1e-13 * max |oracle| per field;
+  * FP64 time stepping: relative L2 per field <= 1e-12 after 100 steps;
+  * FP32 state with FP64 velocity solve: relative L2 per field <= 1e-5 after
+    1000 steps.
+Relative L2 uses the orthonormal basis: ||a - b|| / ||b|| over all
+coefficients (all triangles have the same |det B| on the uniform mesh).
+"""
+import numpy as np
+import pytest
+
+from paper_1904_08684_gb300 import binding as B
+from paper_1904_08684_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+    yield
+    torch.cuda.synchronize()
+
+
+def _relL2(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300)
+
+
+def _state(o, wl, U0=0.0, V0=0.0, with_flow=True):
+    """oracle-projected inputs of a workload; optional smooth discharge"""
+    hb = o.project_hb(wl.hb)
+    xi = o.project(wl.xi0)
+    if with_flow:
+        U = o.project(lambda x, y: U0 + 0.3 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y))
+        V = o.project(lambda x, y: V0 + 0.2 * np.cos(2 * np.pi * (x + y)))
+    else:
+        U = np.zeros_like(xi)
+        V = np.zeros_like(xi)
+    return hb, xi, U, V
+
+
+def _cfg(wl, precision="fp64", **kw):
+    args = dict(bc=wl.bc, precision=precision, rk_order=wl.rk_order, cfl=wl.cfl, dt=wl.dt, g=wl.g,
+                x0=wl.x0, y0=wl.y0, Lx=wl.Lx, Ly=wl.Ly)
+    args.update(kw)
+    return B.make_config(wl.nx, wl.ny, wl.p, **args)
+
+
+def _to_soa(fields, dtype):
+    """list of (E, K) arrays -> torch (F, K, E) on the GPU"""
+    a = np.stack([np.asarray(f).T for f in fields])
+    return torch.tensor(a, dtype=dtype, device="cuda").contiguous()
+
+
+def _gpu_rhs(cfg, hb, xi, U, V, dtype=torch.float64):
+    ctx = B.dg_init(cfg, hb, xi, U, V)
+    try:
+        st = _to_soa([xi, U, V], dtype)
+        out = torch.empty_like(st)
+        B.dg_rhs(ctx, st, out)
+        torch.cuda.synchronize()
+        return out.double().cpu().numpy().transpose(0, 2, 1)
+    finally:
+        B.dg_destroy(ctx)
+
+
+# ------------------------------------------------------------------ RHS
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("bc", ["periodic", "reflective"])
+def test_rhs_matches_oracle_fp64(oracle_mod, p, bc):
+    """13 x 11 quads = 286 triangles: several 128-thread blocks and a ragged tail."""
+    wl = I.waves_p2_512(n=13, p=p, ngauss=3)
+    wl.ny = 11
+    wl.bc = bc
+    o = oracle_mod.Oracle(wl.nx, wl.ny, p, bc=bc)
+    hb, xi, U, V = _state(o, wl)
+    ref = o.rhs(hb, xi, U, V)
+    got = _gpu_rhs(_cfg(wl), hb, xi, U, V)
+    for f in range(3):
+        scale = np.abs(ref[f]).max()
+        assert np.abs(got[f] - ref[f]).max() <= 1e-13 * scale, (f, np.abs(got[f] - ref[f]).max() / scale)
+
+
+def test_rhs_nonsquare_domain(oracle_mod):
+    """hx != hy exercises the diagonal normal and the adj(B) scaling."""
+    wl = I.waves_p2_512(n=9, p=2, ngauss=2)
+    wl.ny, wl.Lx, wl.Ly = 5, 2.0, 0.7
+    wl.xi0 = I.gaussian_sum([0.05], [0.2], [1.0], [0.35], periodic=False)
+    for bc in ("periodic", "reflective"):
+        o = oracle_mod.Oracle(wl.nx, wl.ny, 2, bc=bc, Lx=2.0, Ly=0.7)
+        hb, xi, U, V = _state(o, wl)
+        ref = o.rhs(hb, xi, U, V)
+        got = _gpu_rhs(_cfg(wl, bc=bc), hb, xi, U, V)
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------------ time stepping
+def test_run_matches_oracle_hump_p1(oracle_mod):
+    """32 x 32 reflective hump, p = 1, SSP-RK2, CFL 0.2, 100 steps."""
+    wl = I.hump_p1_32()
+    o = oracle_mod.Oracle(wl.nx, wl.ny, 1, bc="reflective", rk_order=2, cfl=0.2)
+    hb, xi, U, V = _state(o, wl, with_flow=False)
+    xr, Ur, Vr, tr, _ = o.run(hb, xi, U, V, wl.steps)
+    ctx = B.dg_init(_cfg(wl), hb, xi, U, V)
+    try:
+        t = B.dg_run(ctx, wl.steps)
+        xg, Ug, Vg = B.dg_get_state(ctx, o.E, o.K)
+    finally:
+        B.dg_destroy(ctx)
+    assert abs(t - tr) <= 1e-13 * tr
+    for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr)):
+        assert _relL2(g_, r_) <= 1e-12
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_run_matches_oracle_waves(oracle_mod, p):
+    """periodic waves on sinusoidal bathymetry with a mean flow, SSP-RK3."""
+    wl = I.waves_p2_512(n=16, p=p, ngauss=4)
+    o = oracle_mod.Oracle(wl.nx, wl.ny, p, bc="periodic", rk_order=3, cfl=0.2)
+    hb, xi, U, V = _state(o, wl, U0=0.5, V0=-0.3)
+    xr, Ur, Vr, tr, _ = o.run(hb, xi, U, V, 100)
+    ctx = B.dg_init(_cfg(wl), hb, xi, U, V)
+    try:
+        t = B.dg_run(ctx, 100)
+        xg, Ug, Vg = B.dg_get_state(ctx, o.E, o.K)
+    finally:
+        B.dg_destroy(ctx)
+    assert abs(t - tr) <= 1e-13 * tr
+    for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr)):
+        assert _relL2(g_, r_) <= 1e-12
+
+
+def test_fixed_dt_rk1_step(oracle_mod):
+    """forward Euler with a fixed dt: w' = w + dt R(w) exactly as the oracle."""
+    wl = I.waves_p2_512(n=6, p=2, ngauss=2)
+    wl.rk_order, wl.dt = 1, 1e-4
+    o = oracle_mod.Oracle(6, 6, 2, bc="periodic", rk_order=1, dt=1e-4)
+    hb, xi, U, V = _state(o, wl)
+    xr, Ur, Vr, tr, _ = o.run(hb, xi, U, V, 3)
+    ctx = B.dg_init(_cfg(wl, rk_order=1, dt=1e-4), hb, xi, U, V)
+    try:
+        assert B.dg_rk_step(ctx, want_dt=True) == 1e-4
+        B.dg_rk_step(ctx)
+        t = B.dg_run(ctx, 1)
+        xg, Ug, Vg = B.dg_get_state(ctx, o.E, o.K)
+    finally:
+        B.dg_destroy(ctx)
+    assert abs(t - 3e-4) < 1e-18
+    for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr)):
+        assert _relL2(g_, r_) <= 1e-13
+
+
+# ------------------------------------------------------------------ FP32 state
+@pytest.mark.slow
+def test_fp32_mixed_hump_p3_1000_steps(oracle_mod):
+    """FP32 state and contractions, FP64 velocity solve, p = 3, 1000 SSP-RK3
+    steps against the FP64 oracle: relative L2 per field <= 1e-5."""
+    wl = I.hump_p3_32()
+    o = oracle_mod.Oracle(wl.nx, wl.ny, 3, bc="reflective", rk_order=3, cfl=0.2)
+    hb, xi, U, V = _state(o, wl, with_flow=False)
+    xr, Ur, Vr, tr, _ = o.run(hb, xi, U, V, wl.steps)
+    ctx = B.dg_init(_cfg(wl, precision="fp32"), hb, xi, U, V)
+    try:
+        m0, _ = B.dg_diagnostics(ctx)
+        t = B.dg_run(ctx, wl.steps)
+        m1, _ = B.dg_diagnostics(ctx)
+        xg, Ug, Vg = B.dg_get_state(ctx, o.E, o.K)
+    finally:
+        B.dg_destroy(ctx)
+    assert abs(t - tr) <= 1e-5 * tr
+    errs = [_relL2(g_, r_) for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr))]
+    # xi is measured around its mean state: the hump is the signal
+    assert max(errs) <= 1e-5, errs
+    assert abs(m1 - m0) <= 1e-5 * abs(m0)
+
+
+# ------------------------------------------------------------------ invariants on the GPU
+def test_lake_at_rest_gpu():
+    """xi = 0.1, q = 0 on flat bathymetry stays at rest (1000 steps, FP64)."""
+    wl = I.hump_p1_32(p=2, rk=3)
+    E, K = wl.E, wl.K
+    xi = np.zeros((E, K))
+    xi[:, 0] = 0.1 * np.sqrt(2.0)       # constant 0.1 (phi_1 = sqrt 2)
+    hb = np.zeros((E, K))
+    hb[:, 0] = 10.0 * np.sqrt(2.0)
+    z = np.zeros((E, K))
+    ctx = B.dg_init(_cfg(wl), hb, xi, z, z)
+    try:
+        B.dg_run(ctx, 1000)
+        xg, Ug, Vg = B.dg_get_state(ctx, E, K)
+    finally:
+        B.dg_destroy(ctx)
+    assert np.abs(xg - xi).max() <= 1e-12
+    assert np.abs(Ug).max() <= 1e-12 and np.abs(Vg).max() <= 1e-12
+
+
+def test_deterministic_and_checkpoint_resume(oracle_mod):
+    """Two runs are bit-identical; 2N steps == N steps, save, restore, N steps."""
+    wl = I.waves_p2_512(n=12, p=2, ngauss=3)
+    o = oracle_mod.Oracle(12, 12, 2, bc="periodic")
+    hb, xi, U, V = _state(o, wl)
+    cfg = _cfg(wl)
+    outs = []
+    for _ in range(2):
+        ctx = B.dg_init(cfg, hb, xi, U, V)
+        t = B.dg_run(ctx, 20)
+        outs.append((B.dg_get_state(ctx, o.E, o.K), t))
+        B.dg_destroy(ctx)
+    for a, b in zip(outs[0][0], outs[1][0]):
+        assert np.array_equal(a, b)
+    ctx = B.dg_init(cfg, hb, xi, U, V)
+    t1 = B.dg_run(ctx, 10)
+    saved = B.dg_get_state(ctx, o.E, o.K)
+    B.dg_destroy(ctx)
+    ctx = B.dg_init(cfg, hb, *saved)
+    B.dg_set_state(ctx, *saved, t=t1)
+    t2 = B.dg_run(ctx, 10)
+    res = B.dg_get_state(ctx, o.E, o.K)
+    B.dg_destroy(ctx)
+    assert t2 == outs[0][1]
+    for a, b in zip(res, outs[0][0]):
+        assert np.array_equal(a, b)
+
+
+def test_diagnostics_match_oracle(oracle_mod):
+    wl = I.waves_p2_512(n=10, p=2, ngauss=3)
+    o = oracle_mod.Oracle(10, 10, 2, bc="periodic")
+    hb, xi, U, V = _state(o, wl, U0=0.4)
+    m_ref, e_ref = o.diagnostics(hb, xi, U, V)
+    ctx = B.dg_init(_cfg(wl), hb, xi, U, V)
+    try:
+        m, e = B.dg_diagnostics(ctx)
+    finally:
+        B.dg_destroy(ctx)
+    assert abs(m - m_ref) <= 1e-13 * abs(m_ref)
+    assert abs(e - e_ref) <= 1e-13 * abs(e_ref)
+
+
+def test_setup_projection_exact_on_polynomials(oracle_mod):
+    """dg_project reproduces the oracle's projection of a polynomial of
+    degree p (both exact), and of a smooth field to quadrature accuracy."""
+    for p in (1, 2, 3, 4):
+        cfg = B.make_config(5, 4, p, Lx=1.5, Ly=1.0)
+        o = oracle_mod.Oracle(5, 4, p, bc="periodic", Lx=1.5, Ly=1.0)
+        f = lambda x, y: 1.0 + 0.5 * x - 0.25 * y + 0.3 * x * y ** (p - 1)  # noqa: E731
+        Q = B.dg_proj_num_nodes(p)
+        E = o.E
+        xy = torch.empty((2, Q, E), dtype=torch.float64, device="cuda")
+        B.dg_proj_nodes(cfg, xy)
+        vals = f(xy[0], xy[1]).contiguous()
+        coef = torch.empty((o.K, E), dtype=torch.float64, device="cuda")
+        B.dg_project(cfg, vals, coef)
+        torch.cuda.synchronize()
+        got = coef.cpu().numpy().T
+        ref = o.project(f)
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_dry_state_is_reported():
+    """A negative depth in the input is reported as DG_ERR_DRY, not a hang or
+    a fault, and the context stays usable."""
+    wl = I.hump_p1_32(n=8)
+    E, K = wl.E, wl.K
+    xi = np.zeros((E, K))
+    hb = np.zeros((E, K))
+    hb[:, 0] = 10.0 * np.sqrt(2.0)
+    hb[5, 0] = -3.0 * np.sqrt(2.0)      # one element with negative depth
+    z = np.zeros((E, K))
+    ctx = B.dg_init(_cfg(wl, dt=1e-4), hb, xi, z, z)
+    try:
+        with pytest.raises(B.DGError) as ei:
+            B.dg_run(ctx, 1)
+        assert ei.value.status in (B.DG_ERR_DRY, B.DG_ERR_NONFINITE)
+        xg, _, _ = B.dg_get_state(ctx, E, K)
+        assert xg.shape == (E, K)
+    finally:
+        B.dg_destroy(ctx)

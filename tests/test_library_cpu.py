@@ -1,0 +1,86 @@
+"""CPU-side checks of the C-ABI library: it builds, loads and exports every
+entry point declared in include/dgswe.h; argument validation needs no GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "dgswe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(dg_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1904_08684_gb300 import binding
+    return binding.load()
+
+
+def test_header_lists_the_abi():
+    names = _declared()
+    for n in ("dg_init", "dg_rhs", "dg_rk_step", "dg_run"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_1904_08684_gb300 import binding
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.library_path()],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(dg_[a-z_0-9]+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    assert set(binding.EXPORTS) <= exported
+    for n in _declared():
+        assert hasattr(lib, n)
+
+
+def test_counts_and_status_strings(lib):
+    from paper_1904_08684_gb300 import binding as B
+    assert [B.dg_num_basis(p) for p in range(5)] == [1, 3, 6, 10, 15]
+    assert B.dg_num_basis(5) == 0
+    assert B.dg_num_elements(B.make_config(7, 5, 2)) == 70
+    assert B.dg_proj_num_nodes(2) == 25
+    assert B.dg_status_str(B.DG_ERR_DRY) == "DG_ERR_DRY"
+    assert B.dg_status_str(99) == "DG_ERR_UNKNOWN"
+
+
+def test_config_struct_layout(lib):
+    from paper_1904_08684_gb300 import binding as B
+    # int,int | 4 double | ptr | int(+pad) | double | 3 int(+pad) | 2 double | 2 int
+    assert ctypes.sizeof(B.dg_config) == 104
+    assert B.dg_config.g.offset == 56 and B.dg_config.cfl.offset == 80
+
+
+@pytest.mark.parametrize("bad", [dict(nx=0), dict(p=5), dict(rk_order=4), dict(Lx=-1.0),
+                                 dict(cfl=0.0, dt=0.0), dict(block_size=33)])
+def test_invalid_configs_rejected_without_gpu(lib, bad):
+    """Validation happens before any CUDA call, so these run on a CPU host."""
+    from paper_1904_08684_gb300 import binding as B
+    kw = dict(nx=4, ny=4, p=1, bc="periodic")
+    kw.update(bad)
+    cfg = B.make_config(**kw)
+    h = ctypes.c_void_p()
+    z = (ctypes.c_double * 1)()
+    assert B.load().dg_init(ctypes.byref(cfg), z, z, z, z, None, ctypes.byref(h)) == B.DG_ERR_ARG
+    assert B.load().dg_init(None, z, z, z, z, None, ctypes.byref(h)) == B.DG_ERR_ARG
+
+
+def test_unsupported_configs(lib):
+    import numpy as np
+    from paper_1904_08684_gb300 import binding as B
+    for kw in (dict(p=0), dict(bc="dirichlet")):
+        base = dict(nx=4, ny=4, p=1, bc="periodic")
+        base.update(kw)
+        cfg = B.make_config(**base)
+        n = B.dg_num_elements(cfg) * B.dg_num_basis(cfg.p)
+        z = np.zeros(n)
+        with pytest.raises(B.DGError) as ei:
+            B.dg_init(cfg, z, z, z, z)
+        assert ei.value.status == B.DG_ERR_UNSUPPORTED
