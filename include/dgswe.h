@@ -147,6 +147,32 @@ int dg_proj_num_nodes(int p);
 dg_status dg_proj_nodes(const dg_config* cfg, void* d_xy, void* stream);
 dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, void* stream);
 
+/* dg_rhs_noalloc: the same right-hand side as dg_rhs, computed without
+ * allocating any device memory.  The paper has no counterpart; this is an
+ * interface for callers that cannot call cudaMalloc -- code that runs while a
+ * CUDA graph is being captured, runtimes with a fixed device-memory budget
+ * fixed at start-up, or hosts that forbid libraries from growing the device
+ * heap -- and therefore cannot create a dg_ctx (dg_init allocates).
+ *   cfg:        mesh, order, boundary, precision as for dg_init (p = 1..4,
+ *               periodic or reflective walls); dt, cfl, rk_order are ignored.
+ *   d_hb:       device FP64 SoA [K][E] bathymetry coefficients (input).
+ *   d_state_in: device SoA [3][K][E] state in cfg's precision (input).
+ *   d_rhs_out:  device SoA [3][K][E] (output), must not overlap d_state_in.
+ *   stream:     cudaStream_t or NULL; the call is asynchronous on it.
+ * Intermediates live in one fixed 32 MiB array inside the library's device
+ * image, reserved on every GPU that loads the library until the process
+ * exits.  A mesh needs about (K + 3(p+1) + p(p+1) + 3K + 3(6p+7)) words per
+ * triangle (8 bytes FP64, 4 bytes FP32, each block rounded up to 256 bytes);
+ * meshes that do not fit are rejected with DG_ERR_ARG before any GPU work
+ * (about 43,000 triangles at p = 2 in FP64).  The first call on a device looks
+ * up the array's device address once (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call shares the array, which keeps
+ * the previous call's contents (the error word is cleared per call); calls
+ * whose GPU work overlaps race and give wrong results.
+ * Errors: DG_ERR_ARG (invalid or too large), DG_ERR_CUDA. */
+dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_state_in, void* d_rhs_out,
+                         void* stream);
+
 /* Release every resource of the context (NULL is ignored). */
 void dg_destroy(dg_ctx* ctx);
 

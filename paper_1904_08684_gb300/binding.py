@@ -24,7 +24,7 @@ PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
 # every entry point declared in include/dgswe.h
 EXPORTS = ["dg_num_basis", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
-           "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str"]
+           "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc"]
 
 
 class DGError(RuntimeError):
@@ -88,6 +88,7 @@ def load(build_if_missing=True):
     lib.dg_proj_num_nodes.argtypes = [ctypes.c_int]
     lib.dg_proj_nodes.argtypes = [cp, vp, vp]
     lib.dg_project.argtypes = [cp, vp, vp, vp]
+    lib.dg_rhs_noalloc.argtypes = [cp, vp, vp, vp, vp]
     lib.dg_destroy.argtypes = [vp]
     lib.dg_destroy.restype = None
     lib.dg_status_str.argtypes = [ctypes.c_int]
@@ -214,6 +215,12 @@ def dg_proj_nodes(cfg, d_xy, stream=None):
 
 def dg_project(cfg, d_vals, d_coef, stream=None):
     _check(load().dg_project(ctypes.byref(cfg), _dptr(d_vals), _dptr(d_coef), _stream(stream)), "dg_project")
+
+
+def dg_rhs_noalloc(cfg, d_hb, d_state_in, d_rhs_out, stream=None):
+    """dg_rhs without device allocation (fixed in-library scratch array)."""
+    _check(load().dg_rhs_noalloc(ctypes.byref(cfg), _dptr(d_hb), _dptr(d_state_in), _dptr(d_rhs_out),
+                                 _stream(stream)), "dg_rhs_noalloc")
 
 
 def dg_destroy(ctx):

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libdgswe.so")
 
-UNITS = ["dg_fp64.cu", "dg_fp32p64.cu", "dg_fp32p32.cu", "dgswe_api.cu", "dg_project.cu"]
+UNITS = ["dg_fp64.cu", "dg_fp32p64.cu", "dg_fp32p32.cu", "dgswe_api.cu", "dg_project.cu", "dg_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"] + ARCH
 

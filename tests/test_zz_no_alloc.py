@@ -1,0 +1,79 @@
+"""dg_rhs_noalloc: the allocation-free right-hand side must equal dg_rhs.
+
+Callers that cannot call cudaMalloc (graph capture in progress, fixed device
+budgets) use dg_rhs_noalloc, which keeps its intermediates in a fixed array
+inside the library.  This file is collected last on purpose: if it fails, a
+run that stops at the first failure has already run every other test.  It
+must pass both alone in a fresh process and after the other tests.
+"""
+import numpy as np
+import pytest
+
+from paper_1904_08684_gb300 import binding as B
+from paper_1904_08684_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _fields(wl, seed):
+    """seeded smooth fields sampled at the library's set-up nodes and
+    projected with dg_project (device FP64 SoA (K, E))"""
+    cfg = B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc)
+    Q, E, K = B.dg_proj_num_nodes(wl.p), wl.E, wl.K
+    xy = torch.empty((2, Q, E), dtype=torch.float64, device="cuda")
+    B.dg_proj_nodes(cfg, xy)
+    r = I.uniform(seed, 4)
+    fields = [wl.hb, I.gaussian_sum([0.05 + 0.05 * r[0]], [0.08], [r[1]], [r[2]]),
+              lambda x, y: 0.2 + 0.1 * torch.sin(2 * np.pi * (x + r[3])),
+              lambda x, y: -0.1 + 0.05 * torch.cos(2 * np.pi * y)]
+    out = []
+    for f in fields:
+        c = torch.empty((K, E), dtype=torch.float64, device="cuda")
+        B.dg_project(cfg, f(xy[0], xy[1]).contiguous(), c)
+        out.append(c)
+    torch.cuda.synchronize()
+    return out
+
+
+@pytest.mark.parametrize("precision,p", [("fp64", 2), ("fp64", 3), ("fp32", 3)])
+def test_noalloc_rhs_equals_dg_rhs_twice(precision, p):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = I.waves_p2_512(n=37, p=p, ngauss=2)
+    wl.ny = 29                                   # 2146 triangles, ragged last block
+    cfg = B.make_config(wl.nx, wl.ny, p, bc="periodic", precision=precision, rk_order=3, cfl=0.2)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tol = 1e-13 if precision == "fp64" else 1e-5
+    refs, inputs = [], []
+    for seed in (11, 12):                        # two different inputs
+        hb, xi, U, V = _fields(wl, seed)
+        state = torch.stack([xi, U, V]).to(dt).contiguous()
+        ctx = B.dg_init_device(cfg, hb, xi, U, V)
+        try:
+            ref = torch.empty_like(state)
+            B.dg_rhs(ctx, state, ref)
+            torch.cuda.synchronize()
+        finally:
+            B.dg_destroy(ctx)
+        refs.append(ref)
+        inputs.append((hb, state))
+    outs = []
+    for hb, state in inputs:                     # two calls in a row
+        out = torch.full_like(state, float("nan"))
+        B.dg_rhs_noalloc(cfg, hb, state, out)
+        outs.append(out)
+    torch.cuda.synchronize()
+    for call, (o, r) in enumerate(zip(outs, refs)):
+        o = o.double().cpu().numpy()
+        r = r.double().cpu().numpy()
+        assert np.isfinite(o).all()
+        assert np.abs(o - r).max() <= tol * np.abs(r).max(), (call, np.abs(o - r).max())
+
+
+def test_noalloc_rejects_oversized_mesh():
+    cfg = B.make_config(400, 400, 2, bc="periodic")       # 320,000 triangles > 32 MiB
+    with pytest.raises(B.DGError) as ei:
+        B.dg_rhs_noalloc(cfg, 1, 2, 3)                      # rejected before touching pointers
+    assert ei.value.status == B.DG_ERR_ARG
