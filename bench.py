@@ -44,6 +44,8 @@ WORKLOADS = {
     "waves-p4-2048": lambda: I.waves_p4_2048(),
     "waves-p2-512-fp32": lambda: I.waves_p2_512(precision="fp32"),
     "waves-p3-512-fp32": lambda: I.waves_p2_512(p=3, precision="fp32"),
+    "ensemble-256": lambda: I.ensemble(),
+    "ensemble-256-fp64": lambda: I.ensemble(precision="fp64"),
 }
 
 
@@ -114,6 +116,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def _measured_traffic(workload, src_hash):
+    """DRAM bytes per stage launch from the last ncu capture of this exact
+    kernel source (profiles/traffic.json), else None"""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(workload)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("src") != src_hash:
+        return None
+    return rec.get("bytes_per_launch")
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -142,6 +157,114 @@ def _setup_device_inputs(B, torch, wl, cfg, stream):
     return coef[0], coef[1], zero, zero
 
 
+def _cfg_of(B, wl, args):
+    return B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc, precision=wl.precision, rk_order=wl.rk_order,
+                         cfl=wl.cfl, dt=wl.dt, g=wl.g, x0=wl.x0, y0=wl.y0, Lx=wl.Lx, Ly=wl.Ly,
+                         proj_precision=args.proj, block_size=args.block)
+
+
+def run_batch(args, wls):
+    """ensemble of independent instances, one persistent launch per stage"""
+    import torch
+    from paper_1904_08684_gb300 import binding as B
+    from paper_1904_08684_gb300 import flops as FL
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.load()
+    stream = torch.cuda.current_stream()
+    cfgs, fields = [], [[], [], [], []]
+    for wl in wls:
+        cfg = _cfg_of(B, wl, args)
+        f = _setup_device_inputs(B, torch, wl, cfg, stream)
+        cfgs.append(cfg)
+        for k in range(4):
+            fields[k].append(f[k])
+    b = B.dg_batch_init(cfgs, *fields, stream=stream)
+    del fields
+    torch.cuda.empty_cache()
+    S = wls[0].rk_order
+    dofs = B.dg_batch_dofs(b)
+    try:
+        block, tune_ms = B.dg_batch_autotune(b, 2)
+        B.dg_batch_run(b, args.warmup)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            tvals = B.dg_batch_run(b, args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            tt = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            ms = float(tt.item())
+        # end to end: copy every instance's state back to the host each step
+        n_e2e = max(1, min(args.steps, args.e2e_steps))
+        d2h = 0
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            B.dg_batch_run(b, 1)
+            for i, wl in enumerate(wls):
+                B.dg_batch_get_state(b, i, wl.E, wl.K)
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        d2h = sum(3 * wl.K * wl.E * 8 for wl in wls)
+    finally:
+        B.dg_batch_destroy(b)
+    step_ms = ms / args.steps
+    launch_s = step_ms * 1e-3 / S
+    fp64 = wls[0].precision == "fp64"
+    word = 8 if fp64 else 4
+    f64 = sum(2 * FL.SURVEY_FMA[wl.p][0] * wl.E for wl in wls)
+    frest = sum(2 * FL.SURVEY_FMA[wl.p][1] * wl.E for wl in wls)
+    peaks = _peaks()
+    hbm_peak = peaks.get("hbm_gbs")
+    alg_bytes = sum(FL.stage_bytes(wl.p, word) * wl.E for wl in wls)
+    if fp64:
+        ach, peak, what = (f64 + frest) / launch_s / 1e12, FP64_PEAK_TFLOPS, "all FP64 flops"
+    else:
+        ach, peak, what = f64 / launch_s / 1e12, FP64_PEAK_TFLOPS, "FP64 flops of the velocity solve"
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": _measured_traffic("ensemble-256" if not fp64 else "ensemble-256-fp64", FL.source_hash()),
+            "counted": what, "peak_source": "FP64 1.25 TFLOP/s nominal (recipe table)",
+            "fp32_achieved_tflops": None if fp64 else frest / launch_s / 1e12,
+            "fp32_frac": None if fp64 else frest / launch_s / 1e12 / FP32_PEAK_TFLOPS,
+            "hbm_achieved_gbs": alg_bytes / launch_s / 1e9,
+            "hbm_frac_of_measured": (alg_bytes / launch_s / 1e9) / hbm_peak if hbm_peak else None}
+    out = {"metric": METRIC, "value": world * dofs * S / (step_ms * 1e-3), "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if fp64 else ("f32+f64solve" if args.proj == "fp64" else "f32"),
+           "data": "synthetic (seeded SplitMix64 fields, projected on device)",
+           "config": {"workload": "ensemble-%d" % len(wls), "instances": len(wls),
+                      "elements": sum(wl.E for wl in wls),
+                      "p_counts": {str(q): sum(1 for wl in wls if wl.p == q) for q in (1, 2, 3)},
+                      "dof_per_stage": dofs, "rk_stages": S, "precision": wls[0].precision,
+                      "block": block, "autotune_ms_per_step": {str(bb): float(m) for bb, m in
+                                                               zip((32, 64, 96, 128), tune_ms)},
+                      "l2": "working set per stage > L2 (no flush)",
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "gpu_launches": S * args.steps, "roofline": roof,
+           "e2e": {"value": dofs * S / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+           "clocks": clk.summary(), "sim_time_range": [float(min(tvals)), float(max(tvals))]}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        picks = [next(wl for wl in wls if wl.p == q) for q in (1, 2, 3) if any(w.p == q for w in wls)]
+        parts = [cpu_baseline(wl, args.cpu_seconds / len(picks)) for wl in picks]
+        out["cpu_baseline"] = {"value": sum(pp["value"] for pp in parts) / len(parts), "unit": UNIT,
+                               "cores": parts[0]["cores"], "kind": "oracle",
+                               "sample": "; ".join(pp["sample"] for pp in parts) + " (mean of the p classes)"}
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def run_ours(args):
     import torch
     from paper_1904_08684_gb300 import binding as B
@@ -153,9 +276,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.load()
     wl = WORKLOADS[args.workload]()
-    cfg = B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc, precision=wl.precision, rk_order=wl.rk_order,
-                        cfl=wl.cfl, dt=wl.dt, g=wl.g, x0=wl.x0, y0=wl.y0, Lx=wl.Lx, Ly=wl.Ly,
-                        proj_precision=args.proj, block_size=args.block)
+    cfg = _cfg_of(B, wl, args)
     stream = torch.cuda.current_stream()
     hb, xi, qx, qy = _setup_device_inputs(B, torch, wl, cfg, stream)
     ctx = B.dg_init_device(cfg, hb, xi, qx, qy, stream)
@@ -204,15 +325,16 @@ def run_ours(args):
     launch_s = step_ms * 1e-3 / S
     fp64 = wl.precision == "fp64"
     word = 8 if fp64 else 4
-    flop = FL.stage_flops(wl.p) * wl.E
+    flop = FL.algorithmic_flops(wl.p) * wl.E
     peaks = _peaks()
     hbm_peak = peaks.get("hbm_gbs")
     alg_bytes = FL.stage_bytes(wl.p, word) * wl.E
     roof = {"bound": "alu", "achieved": flop / launch_s / 1e12,
             "peak": FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "traffic": None,
+            "traffic": _measured_traffic(wl.name, FL.source_hash()),
             "peak_source": ("FP64 1.25 TFLOP/s nominal (recipe table)" if fp64 else
                             "FP32 152 SM x 128 lanes x 2 x 2.07 GHz"),
+            "flops_per_element_stage": FL.algorithmic_flops(wl.p),
             "hbm_achieved_gbs": alg_bytes / launch_s / 1e9,
             "hbm_frac_of_measured": (alg_bytes / launch_s / 1e9) / hbm_peak if hbm_peak else None}
     roof["frac"] = roof["achieved"] / roof["peak"]
@@ -311,10 +433,14 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instances", type=int, default=0, help="ensemble: use only the first N instances")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # timing rule: at least 3 untimed steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload.startswith("ensemble"):
+        wls = WORKLOADS[args.workload]()
+        run_batch(args, wls[:args.instances] if args.instances > 0 else wls)
     else:
         run_ours(args)
 

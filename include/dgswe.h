@@ -84,6 +84,8 @@ typedef struct {
                               DG_PREC_FP64 always solves in FP64)             */
   int block_size;          /* threads per block of the stage kernels: 0 (=128),
                               32, 64, 96 or 128                               */
+  double tau_bf;           /* bottom friction coefficient of Eq. (2) (>= 0)    */
+  double f_c;              /* Coriolis coefficient of Eq. (2)                  */
 } dg_config;
 
 typedef struct dg_ctx dg_ctx;
@@ -172,6 +174,43 @@ dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, voi
  * Errors: DG_ERR_ARG (invalid or too large), DG_ERR_CUDA. */
 dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_state_in, void* d_rhs_out,
                          void* stream);
+
+/* ---- batched instances -------------------------------------------------
+ * Many independent problems of uneven size and order (ensembles of
+ * bathymetries and initial states) advanced together: one persistent kernel
+ * launch per RK stage covers every instance, each instance keeps its own CFL
+ * time step and time, and each step is one captured CUDA graph.  The
+ * per-instance arithmetic is the single-instance scheme above (same kernels'
+ * element code), so results equal those of separate dg_init contexts. */
+typedef struct dg_batch dg_batch;
+
+/* n instances; cfgs[i] as for dg_init with p = 1..3 and nx, ny >= 2.  All
+ * instances share precision, proj_precision, rk_order and fixed-vs-CFL time
+ * stepping (else DG_ERR_ARG).  d_hb[i], d_xi[i], d_qx[i], d_qy[i]: DEVICE
+ * FP64 SoA [K_i][E_i] arrays (copied).  Errors: DG_ERR_ARG,
+ * DG_ERR_UNSUPPORTED (p = 4, Dirichlet), DG_ERR_OOM, DG_ERR_CUDA. */
+dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
+                        const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out);
+
+/* nsteps steps of every instance; t_out (NULL or n doubles) receives each
+ * instance's time.  Synchronises the stream once at the end. */
+dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out);
+
+/* state of instance i as host FP64 AoS [E_i][K_i] arrays (each may be NULL) */
+dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy);
+
+/* Autotuner: times trial_steps steps with 32, 64, 96 and 128 elements per
+ * work item (one thread per element), restores the state, keeps the fastest;
+ * *block_out gets it and ms_out (NULL or 4 doubles) the ms per step of each. */
+dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out);
+
+/* set the elements per work item (32, 64, 96 or 128) */
+dg_status dg_batch_set_block(dg_batch* b, int block);
+
+/* degrees of freedom updated per RK stage: sum over instances of 3 K E */
+long long dg_batch_dofs(const dg_batch* b);
+
+void dg_batch_destroy(dg_batch* b);
 
 /* Release every resource of the context (NULL is ignored). */
 void dg_destroy(dg_ctx* ctx);

@@ -24,7 +24,9 @@ PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
 # every entry point declared in include/dgswe.h
 EXPORTS = ["dg_num_basis", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
-           "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc"]
+           "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc",
+           "dg_batch_init", "dg_batch_run", "dg_batch_get_state", "dg_batch_autotune", "dg_batch_set_block",
+           "dg_batch_dofs", "dg_batch_destroy"]
 
 
 class DGError(RuntimeError):
@@ -41,16 +43,18 @@ class dg_config(ctypes.Structure):
                 ("p", ctypes.c_int), ("g", ctypes.c_double),
                 ("bc", ctypes.c_int), ("precision", ctypes.c_int), ("rk_order", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
-                ("proj_precision", ctypes.c_int), ("block_size", ctypes.c_int)]
+                ("proj_precision", ctypes.c_int), ("block_size", ctypes.c_int),
+                ("tau_bf", ctypes.c_double), ("f_c", ctypes.c_double)]
 
 
 def make_config(nx, ny, p, bc="periodic", precision="fp64", rk_order=3, cfl=0.2, dt=0.0, g=9.81,
-                x0=0.0, y0=0.0, Lx=1.0, Ly=1.0, proj_precision="fp64", block_size=0):
+                x0=0.0, y0=0.0, Lx=1.0, Ly=1.0, proj_precision="fp64", block_size=0, tau_bf=0.0, f_c=0.0):
     return dg_config(nx, ny, x0, y0, Lx, Ly, None, p, g,
                      BC[bc] if isinstance(bc, str) else int(bc),
                      PREC[precision] if isinstance(precision, str) else int(precision),
                      rk_order, cfl, dt,
-                     DG_PROJ_FP32 if proj_precision == "fp32" else DG_PROJ_FP64, block_size)
+                     DG_PROJ_FP32 if proj_precision == "fp32" else DG_PROJ_FP64, block_size,
+                     float(tau_bf), float(f_c))
 
 
 _lib = None
@@ -89,6 +93,16 @@ def load(build_if_missing=True):
     lib.dg_proj_nodes.argtypes = [cp, vp, vp]
     lib.dg_project.argtypes = [cp, vp, vp, vp]
     lib.dg_rhs_noalloc.argtypes = [cp, vp, vp, vp, vp]
+    vpp = ctypes.POINTER(ctypes.c_void_p)
+    lib.dg_batch_init.argtypes = [ctypes.c_int, cp, vpp, vpp, vpp, vpp, vp, ctypes.POINTER(vp)]
+    lib.dg_batch_run.argtypes = [vp, ctypes.c_int, dp]
+    lib.dg_batch_get_state.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+    lib.dg_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
+    lib.dg_batch_set_block.argtypes = [vp, ctypes.c_int]
+    lib.dg_batch_dofs.argtypes = [vp]
+    lib.dg_batch_dofs.restype = ctypes.c_longlong
+    lib.dg_batch_destroy.argtypes = [vp]
+    lib.dg_batch_destroy.restype = None
     lib.dg_destroy.argtypes = [vp]
     lib.dg_destroy.restype = None
     lib.dg_status_str.argtypes = [ctypes.c_int]
@@ -221,6 +235,56 @@ def dg_rhs_noalloc(cfg, d_hb, d_state_in, d_rhs_out, stream=None):
     """dg_rhs without device allocation (fixed in-library scratch array)."""
     _check(load().dg_rhs_noalloc(ctypes.byref(cfg), _dptr(d_hb), _dptr(d_state_in), _dptr(d_rhs_out),
                                  _stream(stream)), "dg_rhs_noalloc")
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for k, t in enumerate(ts):
+        arr[k] = t if isinstance(t, int) else t.data_ptr()
+    return arr
+
+
+def dg_batch_init(cfgs, d_hb, d_xi, d_qx, d_qy, stream=None):
+    """Batch of instances from device FP64 (K_i, E_i) arrays (lists)."""
+    n = len(cfgs)
+    carr = (dg_config * n)(*cfgs)
+    h = ctypes.c_void_p()
+    _check(load().dg_batch_init(n, carr, _ptr_array(d_hb), _ptr_array(d_xi), _ptr_array(d_qx),
+                                _ptr_array(d_qy), _stream(stream), ctypes.byref(h)), "dg_batch_init")
+    h._n = n
+    return h
+
+
+def dg_batch_run(b, nsteps):
+    t = np.zeros(b._n)
+    _check(load().dg_batch_run(b, int(nsteps), _hptr(t)), "dg_batch_run")
+    return t
+
+
+def dg_batch_get_state(b, i, E, K):
+    out = [np.zeros((E, K)) for _ in range(3)]
+    _check(load().dg_batch_get_state(b, int(i), *[_hptr(a) for a in out]), "dg_batch_get_state")
+    return out
+
+
+def dg_batch_autotune(b, trial_steps=2):
+    blk = ctypes.c_int(0)
+    ms = np.zeros(4)
+    _check(load().dg_batch_autotune(b, int(trial_steps), ctypes.byref(blk), _hptr(ms)), "dg_batch_autotune")
+    return blk.value, ms
+
+
+def dg_batch_set_block(b, block):
+    _check(load().dg_batch_set_block(b, int(block)), "dg_batch_set_block")
+
+
+def dg_batch_dofs(b):
+    return load().dg_batch_dofs(b)
+
+
+def dg_batch_destroy(b):
+    if b:
+        load().dg_batch_destroy(b)
 
 
 def dg_destroy(ctx):

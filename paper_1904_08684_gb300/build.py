@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libdgswe.so")
 
-UNITS = ["dg_fp64.cu", "dg_fp32p64.cu", "dg_fp32p32.cu", "dgswe_api.cu", "dg_project.cu", "dg_noalloc.cu"]
+UNITS = ["dg_fp64.cu", "dg_fp32p64.cu", "dg_fp32p32.cu", "dgswe_api.cu", "dg_project.cu", "dg_noalloc.cu",
+         "dg_batch_fp64.cu", "dg_batch_fp32p64.cu", "dg_batch_fp32p32.cu", "dg_batch_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"] + ARCH
 
@@ -30,7 +31,7 @@ def _nvcc():
 
 def _sources():
     out = [os.path.join(CSRC, u) for u in UNITS]
-    out += [os.path.join(CSRC, f) for f in ("dg_kernels.cuh", "dg_launch.cuh", "gen_tables.py")]
+    out += [os.path.join(CSRC, f) for f in ("dg_kernels.cuh", "dg_launch.cuh", "dg_batch.cuh", "gen_tables.py")]
     out.append(os.path.join(INCLUDE, "dgswe.h"))
     return out
 

@@ -1,0 +1,147 @@
+// dg_batch.cuh -- many independent instances (uneven mesh sizes and orders
+// p = 1..3) advanced by one persistent launch per RK stage.
+//
+// Work items are (instance, first element) blocks of blockDim elements,
+// ordered by decreasing p (the most expensive work first).  Each CTA pulls
+// items from a global counter until none is left; every element's work is
+// independent of which CTA does it, so results are deterministic and equal
+// to the single-instance kernels (stage_element is shared).  Each instance
+// has its own CFL time step: the wave-speed maximum of an item goes to its
+// instance's slot.
+#pragma once
+
+#include "dg_kernels.cuh"
+
+namespace dgswe {
+
+// device descriptor of one instance
+struct BatchInst {
+  Mesh m;
+  double g, inv_det, cfl_num, dt_fixed;
+  double det, tau_bf, f_c;
+  void* w[3];          // state buffers (instance's own SoA arrays)
+  void* vs[2];
+  void* rec[2];
+  const void* hb;
+  const void* hbt;
+  const void* ghb;
+  double* lam;         // slot s of this instance at lam[s * n_inst]
+  double* t;
+  int p;
+};
+
+struct BatchItem {
+  int inst;
+  int start;
+};
+
+struct BatchArgs {
+  const BatchInst* inst;
+  const BatchItem* items;
+  int n_items, n_inst;
+  unsigned* counter;   // zeroed before the launch
+  unsigned* err;
+  int win, wout, pin;  // state in/out buffer, evaluation buffer read (MODE_STAGE)
+  double alpha, beta;
+  int lc;              // wave-speed slot of the current step
+  int last;            // last stage: wave speed -> slot 1-lc, t += dt
+};
+
+template <class Real, class PR, int MODE>
+__global__ void __launch_bounds__(128) batch_kernel(const BatchArgs a) {
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= a.n_items) break;
+    const BatchItem item = a.items[it];
+    const BatchInst& d = a.inst[item.inst];
+    StageParams<Real> sp;
+    sp.m = d.m;
+    sp.g = Real(d.g);
+    sp.hb = static_cast<const Real*>(d.hb);
+    sp.hbt = static_cast<const Real*>(d.hbt);
+    sp.ghb = static_cast<const Real*>(d.ghb);
+    sp.inv_det = d.inv_det;
+    sp.det = d.det;
+    sp.tau_bf = d.tau_bf;
+    sp.f_c = d.f_c;
+    sp.err = a.err;
+    sp.dt_fixed = d.dt_fixed;
+    sp.cfl_num = d.cfl_num;
+    sp.alpha = a.alpha;
+    sp.beta = a.beta;
+    sp.w0 = static_cast<const Real*>(d.w[0]);
+    sp.rhs_out = nullptr;
+    sp.lam_clear = nullptr;
+    sp.t = nullptr;
+    double* lam_target = nullptr;
+    double dt = 0.0;
+    if constexpr (MODE == MODE_EVAL) {
+      sp.w = static_cast<const Real*>(d.w[0]);
+      sp.vs = nullptr;
+      sp.rec = nullptr;
+      sp.vs_out = static_cast<Real*>(d.vs[a.pin]);
+      sp.rec_out = static_cast<Real*>(d.rec[a.pin]);
+      sp.wout = nullptr;
+      sp.lam = nullptr;
+      lam_target = d.lam + (long long)a.lc * a.n_inst;
+    } else {
+      sp.w = static_cast<const Real*>(d.w[a.win]);
+      sp.wout = static_cast<Real*>(d.w[a.wout]);
+      sp.vs = static_cast<const Real*>(d.vs[a.pin]);
+      sp.rec = static_cast<const Real*>(d.rec[a.pin]);
+      sp.vs_out = static_cast<Real*>(d.vs[1 - a.pin]);
+      sp.rec_out = static_cast<Real*>(d.rec[1 - a.pin]);
+      sp.lam = d.lam + (long long)a.lc * a.n_inst;
+      dt = d.dt_fixed > 0.0 ? d.dt_fixed : d.cfl_num / sp.lam[0];
+      if (a.last && !(d.dt_fixed > 0.0)) lam_target = d.lam + (long long)(1 - a.lc) * a.n_inst;
+    }
+    sp.lam_next = lam_target;
+    const long long e = (long long)item.start + threadIdx.x;
+    double lam_e = 0.0;
+    unsigned err = 0;
+    if (e < d.m.E) {
+      switch (d.p) {
+        case 1: stage_element<1, Real, PR, MODE>(sp, e, dt, lam_e, err); break;
+        case 2: stage_element<2, Real, PR, MODE>(sp, e, dt, lam_e, err); break;
+        default: stage_element<3, Real, PR, MODE>(sp, e, dt, lam_e, err); break;
+      }
+    }
+    if (lam_target) {
+      const double l = block_max(lam_e);
+      if (threadIdx.x == 0) atomic_max_nonneg(lam_target, l);
+    }
+    if (err) atomicOr(a.err, err);
+    if (MODE == MODE_STAGE && a.last && item.start == 0 && threadIdx.x == 0) *d.t += dt;
+  }
+}
+
+cudaError_t batch_launch_fp64(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s);
+cudaError_t batch_launch_fp32p64(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s);
+cudaError_t batch_launch_fp32p32(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s);
+cudaError_t batch_occupancy_fp64(int block, int* blocks_per_sm);
+cudaError_t batch_occupancy_fp32p64(int block, int* blocks_per_sm);
+cudaError_t batch_occupancy_fp32p32(int block, int* blocks_per_sm);
+
+#define DGSWE_DEFINE_BATCH(SUFFIX, REAL, PREAL)                                                       \
+  cudaError_t batch_launch_##SUFFIX(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s) { \
+    if (mode == MODE_EVAL)                                                                            \
+      batch_kernel<REAL, PREAL, MODE_EVAL><<<grid, block, 0, s>>>(a);                                 \
+    else                                                                                              \
+      batch_kernel<REAL, PREAL, MODE_STAGE><<<grid, block, 0, s>>>(a);                                \
+    return cudaGetLastError();                                                                        \
+  }                                                                                                   \
+  cudaError_t batch_occupancy_##SUFFIX(int block, int* blocks_per_sm) {                               \
+    int a = 0, b = 0;                                                                                 \
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                    \
+        &a, batch_kernel<REAL, PREAL, MODE_STAGE>, block, 0);                                         \
+    if (e != cudaSuccess) return e;                                                                   \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel<REAL, PREAL, MODE_EVAL>, block, 0); \
+    *blocks_per_sm = a < b ? a : b;                                                                   \
+    return e;                                                                                         \
+  }
+
+}  // namespace dgswe

@@ -1,0 +1,500 @@
+// dg_batch_api.cu -- C-ABI of batched instances (include/dgswe.h, dg_batch_*):
+// arenas, work items, graph-captured steps and the block-size autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "dg_batch.cuh"
+#include "dg_launch.cuh"
+#include "dgswe.h"
+
+using namespace dgswe;
+
+namespace {
+
+int K_of(int p) { return (p + 1) * (p + 2) / 2; }
+
+dg_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DG_OK;
+  if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+  return DG_ERR_CUDA;
+}
+
+#define CK(x)                                          \
+  do {                                                 \
+    cudaError_t _e = (x);                              \
+    if (_e != cudaSuccess) return cuda_status(_e);     \
+  } while (0)
+
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+const double RK_B[3][3] = {{1.0, 0.0, 0.0}, {1.0, 0.5, 0.0}, {1.0, 0.25, 2.0 / 3.0}};
+
+struct HostInst {
+  dg_config cfg;
+  int p, K, K1, P1, NREC;
+  long long E;
+  size_t o_state, o_rec, o_hb, o_hbt, o_ghb;  // byte offsets in the arenas
+};
+
+}  // namespace
+
+struct dg_batch {
+  int n = 0;
+  int arith = 0;
+  size_t rsz = 0;
+  int S = 0;
+  bool adaptive = false;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  std::vector<HostInst> inst;
+  size_t sz_state = 0, sz_rec = 0;
+  void* w[3] = {nullptr, nullptr, nullptr};
+  void* vs[2] = {nullptr, nullptr};
+  void* rec[2] = {nullptr, nullptr};
+  void* hb = nullptr;
+  void* hbt = nullptr;
+  void* ghb = nullptr;
+  double* lam = nullptr;        // [2][n]
+  double* t = nullptr;          // [n]
+  unsigned* err = nullptr;
+  unsigned* counters = nullptr; // one per launch of a step (+ evaluation)
+  BatchInst* d_inst = nullptr;
+  BatchItem* d_items = nullptr;
+  int n_items = 0;
+  int block = 0, grid = 0;
+  int ep = 0, lc = 0;
+  bool evaluated = false;
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  long long dofs = 0;
+};
+
+namespace {
+
+cudaError_t launch_batch(const dg_batch* b, int mode, const BatchArgs& a, cudaStream_t s) {
+  switch (b->arith) {
+    case ARITH_FP64: return batch_launch_fp64(mode, b->grid, b->block, a, s);
+    case ARITH_FP32_P64: return batch_launch_fp32p64(mode, b->grid, b->block, a, s);
+    default: return batch_launch_fp32p32(mode, b->grid, b->block, a, s);
+  }
+}
+
+BatchArgs base_args(const dg_batch* b) {
+  BatchArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.inst = b->d_inst;
+  a.items = b->d_items;
+  a.n_items = b->n_items;
+  a.n_inst = b->n;
+  a.err = b->err;
+  return a;
+}
+
+dg_status launch_eval(dg_batch* b, cudaStream_t s) {
+  CK(cudaMemsetAsync(b->counters, 0, sizeof(unsigned), s));
+  CK(cudaMemsetAsync(b->lam + (size_t)b->lc * b->n, 0, sizeof(double) * b->n, s));
+  BatchArgs a = base_args(b);
+  a.counter = b->counters;
+  a.pin = b->ep;
+  a.lc = b->lc;
+  CK(launch_batch(b, MODE_EVAL, a, s));
+  return DG_OK;
+}
+
+dg_status launch_step(const dg_batch* b, int ep, int lc, cudaStream_t s) {
+  CK(cudaMemsetAsync(b->counters + 1, 0, sizeof(unsigned) * b->S, s));
+  if (b->adaptive) CK(cudaMemsetAsync(b->lam + (size_t)(1 - lc) * b->n, 0, sizeof(double) * b->n, s));
+  for (int st = 0; st < b->S; ++st) {
+    BatchArgs a = base_args(b);
+    a.counter = b->counters + 1 + st;
+    a.win = st == 0 ? 0 : st;
+    a.wout = st == b->S - 1 ? 0 : st + 1;
+    a.pin = (ep + st) & 1;
+    a.beta = RK_B[b->S - 1][st];
+    a.alpha = 1.0 - a.beta;
+    a.lc = lc;
+    a.last = st == b->S - 1;
+    CK(launch_batch(b, MODE_STAGE, a, s));
+  }
+  return DG_OK;
+}
+
+void drop_graphs(dg_batch* b) {
+  for (auto& row : b->graph)
+    for (auto& g : row)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
+dg_status get_graph(dg_batch* b, cudaGraphExec_t* out) {
+  cudaGraphExec_t& g = b->graph[b->ep][b->lc];
+  if (!g) {
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    dg_status st = launch_step(b, b->ep, b->lc, b->cap);
+    cudaError_t ce = cudaStreamEndCapture(b->cap, &graph);
+    if (st != DG_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return st;
+    }
+    CK(ce);
+    ce = cudaGraphInstantiate(&g, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ce);
+  }
+  *out = g;
+  return DG_OK;
+}
+
+// work items of blockDim elements, most expensive order first
+dg_status build_items(dg_batch* b, int block) {
+  std::vector<BatchItem> items;
+  for (int p = 3; p >= 1; --p)
+    for (int i = 0; i < b->n; ++i) {
+      if (b->inst[i].p != p) continue;
+      for (long long s = 0; s < b->inst[i].E; s += block) items.push_back({i, (int)s});
+    }
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  CK(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
+  CK(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
+  b->n_items = (int)items.size();
+  int occ = 0;
+  cudaError_t e;
+  switch (b->arith) {
+    case ARITH_FP64: e = batch_occupancy_fp64(block, &occ); break;
+    case ARITH_FP32_P64: e = batch_occupancy_fp32p64(block, &occ); break;
+    default: e = batch_occupancy_fp32p32(block, &occ); break;
+  }
+  CK(e);
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  b->block = block;
+  b->grid = std::max(1, std::min(b->n_items, sms * std::max(1, occ)));
+  drop_graphs(b);
+  return DG_OK;
+}
+
+void free_batch(dg_batch* b) {
+  if (!b) return;
+  drop_graphs(b);
+  void* bufs[] = {b->w[0], b->w[1], b->w[2], b->vs[0], b->vs[1], b->rec[0], b->rec[1], b->hb, b->hbt,
+                  b->ghb, b->lam, b->t, b->err, b->counters, b->d_inst, b->d_items};
+  for (void* p : bufs)
+    if (p) cudaFree(p);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+__global__ void cvt_f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = float(a[i]);
+}
+__global__ void cvt_b(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = double(a[i]);
+}
+
+dg_status store_real(const dg_batch* b, const double* src, void* dst, long long n, cudaStream_t s) {
+  if (n <= 0) return DG_OK;
+  if (b->arith == ARITH_FP64) {
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else {
+    cvt_f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, (float*)dst, n);
+    CK(cudaGetLastError());
+  }
+  return DG_OK;
+}
+
+dg_status validate_one(const dg_config* c) {
+  if (c->nx < 2 || c->ny < 2 || c->p < 1 || c->p > 3) return c->p > 3 ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
+  if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
+  if (c->rk_order < 1 || c->rk_order > 3 || c->bc < 0 || c->bc > 2) return DG_ERR_ARG;
+  if (c->bc == DG_BC_DIRICHLET || c->vertex_xy) return DG_ERR_UNSUPPORTED;
+  if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
+  if (2.0 * c->nx * (double)c->ny > 2.0e9) return DG_ERR_ARG;
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
+                        const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out) {
+  if (n < 1 || !cfgs || !d_hb || !d_xi || !d_qx || !d_qy || !out) return DG_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    dg_status s = validate_one(&cfgs[i]);
+    if (s != DG_OK) return s;
+    if (!d_hb[i] || !d_xi[i] || !d_qx[i] || !d_qy[i]) return DG_ERR_ARG;
+    if (cfgs[i].precision != cfgs[0].precision || cfgs[i].proj_precision != cfgs[0].proj_precision ||
+        cfgs[i].rk_order != cfgs[0].rk_order || (cfgs[i].dt > 0.0) != (cfgs[0].dt > 0.0))
+      return DG_ERR_ARG;
+  }
+  dg_batch* b = new (std::nothrow) dg_batch();
+  if (!b) return DG_ERR_OOM;
+  b->n = n;
+  b->arith = cfgs[0].precision == DG_PREC_FP64
+                 ? ARITH_FP64
+                 : (cfgs[0].proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32 : ARITH_FP32_P64);
+  b->rsz = b->arith == ARITH_FP64 ? 8 : 4;
+  b->S = cfgs[0].rk_order;
+  b->adaptive = !(cfgs[0].dt > 0.0);
+  b->stream = (cudaStream_t)stream;
+  size_t ost = 0, orec = 0, ohb = 0, ohbt = 0, oghb = 0;
+  b->dofs = 0;
+  for (int i = 0; i < n; ++i) {
+    HostInst h;
+    h.cfg = cfgs[i];
+    h.p = cfgs[i].p;
+    h.K = K_of(h.p);
+    h.K1 = K_of(h.p - 1);
+    h.P1 = h.p + 1;
+    h.NREC = 6 * h.P1 + 1;
+    h.E = 2LL * cfgs[i].nx * cfgs[i].ny;
+    h.o_state = ost;
+    h.o_rec = orec;
+    h.o_hb = ohb;
+    h.o_hbt = ohbt;
+    h.o_ghb = oghb;
+    ost += align256((size_t)3 * h.K * h.E * b->rsz);
+    orec += align256((size_t)3 * h.NREC * h.E * b->rsz);
+    ohb += align256((size_t)h.K * h.E * b->rsz);
+    ohbt += align256((size_t)3 * h.P1 * h.E * b->rsz);
+    oghb += align256((size_t)2 * h.K1 * h.E * b->rsz);
+    b->dofs += 3LL * h.K * h.E;
+    b->inst.push_back(h);
+  }
+  b->sz_state = ost;
+  b->sz_rec = orec;
+  dg_status st = DG_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (st != DG_OK) return;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) st = cuda_status(e);
+  };
+  for (int k = 0; k < 3; ++k) alloc(&b->w[k], ost);
+  for (int k = 0; k < 2; ++k) {
+    alloc(&b->vs[k], ost);
+    alloc(&b->rec[k], orec);
+  }
+  alloc(&b->hb, ohb);
+  alloc(&b->hbt, ohbt);
+  alloc(&b->ghb, oghb);
+  alloc((void**)&b->lam, sizeof(double) * 2 * n);
+  alloc((void**)&b->t, sizeof(double) * n);
+  alloc((void**)&b->err, sizeof(unsigned));
+  alloc((void**)&b->counters, sizeof(unsigned) * 8);
+  alloc((void**)&b->d_inst, sizeof(BatchInst) * n);
+  if (st == DG_OK) {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  if (st != DG_OK) {
+    free_batch(b);
+    return st;
+  }
+  cudaStream_t s = b->stream;
+  std::vector<BatchInst> desc(n);
+  cudaError_t e = cudaMemsetAsync(b->lam, 0, sizeof(double) * 2 * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->t, 0, sizeof(double) * n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, sizeof(unsigned), s);
+  for (int i = 0; i < n && e == cudaSuccess && st == DG_OK; ++i) {
+    const HostInst& h = b->inst[i];
+    BatchInst& d = desc[i];
+    std::memset(&d, 0, sizeof d);
+    const double hx = h.cfg.Lx / h.cfg.nx, hy = h.cfg.Ly / h.cfg.ny;
+    d.m.nx = h.cfg.nx;
+    d.m.ny = h.cfg.ny;
+    d.m.E = h.E;
+    d.m.hx = hx;
+    d.m.hy = hy;
+    d.m.diag = std::hypot(hx, hy);
+    d.m.periodic = h.cfg.bc == DG_BC_PERIODIC;
+    d.g = h.cfg.g;
+    d.inv_det = 1.0 / (hx * hy);
+    d.det = hx * hy;
+    d.tau_bf = h.cfg.tau_bf;
+    d.f_c = h.cfg.f_c;
+    const double dmin = 4.0 * (0.5 * hx * hy) / (hx + hy + std::hypot(hx, hy));
+    d.cfl_num = h.cfg.cfl * dmin / (2.0 * h.p + 1.0);
+    d.dt_fixed = h.cfg.dt > 0.0 ? h.cfg.dt : 0.0;
+    for (int k = 0; k < 3; ++k) d.w[k] = (char*)b->w[k] + h.o_state;
+    for (int k = 0; k < 2; ++k) {
+      d.vs[k] = (char*)b->vs[k] + h.o_state;
+      d.rec[k] = (char*)b->rec[k] + h.o_rec;
+    }
+    d.hb = (char*)b->hb + h.o_hb;
+    d.hbt = (char*)b->hbt + h.o_hbt;
+    d.ghb = (char*)b->ghb + h.o_ghb;
+    d.lam = b->lam + i;
+    d.t = b->t + i;
+    d.p = h.p;
+    const long long KE = (long long)h.K * h.E;
+    char* w0 = (char*)d.w[0];
+    if ((st = store_real(b, (const double*)d_xi[i], w0, KE, s)) != DG_OK) break;
+    if ((st = store_real(b, (const double*)d_qx[i], w0 + KE * b->rsz, KE, s)) != DG_OK) break;
+    if ((st = store_real(b, (const double*)d_qy[i], w0 + 2 * KE * b->rsz, KE, s)) != DG_OK) break;
+    void *ph = (void*)d.hb, *pt = (void*)d.hbt, *pg = (void*)d.ghb;
+    switch (b->arith) {
+      case ARITH_FP64: e = static_fp64(h.p, d.m, (const double*)d_hb[i], ph, pt, pg, s); break;
+      case ARITH_FP32_P64: e = static_fp32p64(h.p, d.m, (const double*)d_hb[i], ph, pt, pg, s); break;
+      default: e = static_fp32p32(h.p, d.m, (const double*)d_hb[i], ph, pt, pg, s); break;
+    }
+  }
+  if (e == cudaSuccess && st == DG_OK)
+    e = cudaMemcpyAsync(b->d_inst, desc.data(), sizeof(BatchInst) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess || st != DG_OK) {
+    free_batch(b);
+    return st != DG_OK ? st : cuda_status(e);
+  }
+  if ((st = build_items(b, 128)) != DG_OK) {
+    free_batch(b);
+    return st;
+  }
+  *out = b;
+  return DG_OK;
+}
+
+void dg_batch_destroy(dg_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  free_batch(b);
+}
+
+long long dg_batch_dofs(const dg_batch* b) { return b ? b->dofs : 0; }
+
+dg_status dg_batch_set_block(dg_batch* b, int block) {
+  if (!b || block < 32 || block > 128 || block % 32) return DG_ERR_ARG;
+  CK(cudaStreamSynchronize(b->stream));
+  return build_items(b, block);
+}
+
+dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out) {
+  if (!b || nsteps < 0) return DG_ERR_ARG;
+  if (!b->evaluated) {
+    dg_status s = launch_eval(b, b->stream);
+    if (s != DG_OK) return s;
+    b->evaluated = true;
+  }
+  for (int k = 0; k < nsteps; ++k) {
+    cudaGraphExec_t g;
+    dg_status s = get_graph(b, &g);
+    if (s != DG_OK) return s;
+    CK(cudaGraphLaunch(g, b->stream));
+    b->ep = (b->ep + b->S) & 1;
+    if (b->adaptive) b->lc = 1 - b->lc;
+  }
+  unsigned h = 0;
+  CK(cudaMemcpyAsync(&h, b->err, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+  if (t_out) CK(cudaMemcpyAsync(t_out, b->t, sizeof(double) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  if (h) {
+    CK(cudaMemsetAsync(b->err, 0, sizeof(unsigned), b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+  }
+  if (h & ERRF_NONFINITE) return DG_ERR_NONFINITE;
+  if (h & ERRF_DRY) return DG_ERR_DRY;
+  return DG_OK;
+}
+
+dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy) {
+  if (!b || i < 0 || i >= b->n) return DG_ERR_ARG;
+  const HostInst& h = b->inst[i];
+  const long long E = h.E, KE = (long long)h.K * E;
+  std::vector<double> host((size_t)3 * KE);
+  double* tmp = nullptr;
+  CK(cudaMalloc(&tmp, sizeof(double) * 3 * KE));
+  const char* src = (const char*)b->w[0] + h.o_state;
+  cudaError_t e = cudaSuccess;
+  if (b->arith == ARITH_FP64) {
+    e = cudaMemcpyAsync(tmp, src, sizeof(double) * 3 * KE, cudaMemcpyDeviceToDevice, b->stream);
+  } else {
+    cvt_b<<<(unsigned)((3 * KE + 255) / 256), 256, 0, b->stream>>>((const float*)src, tmp, 3 * KE);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(host.data(), tmp, sizeof(double) * 3 * KE, cudaMemcpyDeviceToHost, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  cudaFree(tmp);
+  CK(e);
+  double* dst[3] = {xi, qx, qy};
+  for (int f = 0; f < 3; ++f) {
+    if (!dst[f]) continue;
+    for (long long el = 0; el < E; ++el)
+      for (int k = 0; k < h.K; ++k) dst[f][(size_t)el * h.K + k] = host[(size_t)f * KE + (size_t)k * E + el];
+  }
+  return DG_OK;
+}
+
+// Autotuner: times trial_steps steps at every candidate block size (elements
+// per work item) on the batch's own state, restores the state, keeps the
+// fastest.  ms_out[4] receives the time per step of 32, 64, 96, 128.
+dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out) {
+  if (!b || trial_steps < 1) return DG_ERR_ARG;
+  dg_status s;
+  CK(cudaStreamSynchronize(b->stream));
+  // snapshot of everything a step changes
+  void* save = nullptr;
+  double* save_t = nullptr;
+  CK(cudaMalloc(&save, b->sz_state));
+  CK(cudaMalloc((void**)&save_t, sizeof(double) * 3 * b->n));
+  CK(cudaMemcpyAsync(save, b->w[0], b->sz_state, cudaMemcpyDeviceToDevice, b->stream));
+  CK(cudaMemcpyAsync(save_t, b->t, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, b->stream));
+  const int ep0 = b->ep, lc0 = b->lc;
+  const bool ev0 = b->evaluated;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const int cand[4] = {32, 64, 96, 128};
+  double best = 1e300;
+  int best_block = b->block;
+  for (int c = 0; c < 4; ++c) {
+    if ((s = build_items(b, cand[c])) != DG_OK) return s;
+    b->evaluated = false;
+    b->ep = ep0;
+    b->lc = lc0;
+    if ((s = dg_batch_run(b, 1, nullptr)) != DG_OK) return s;   // warm-up, graph build
+    CK(cudaEventRecord(e0, b->stream));
+    for (int k = 0; k < trial_steps; ++k) {
+      cudaGraphExec_t g;
+      if ((s = get_graph(b, &g)) != DG_OK) return s;
+      CK(cudaGraphLaunch(g, b->stream));
+      b->ep = (b->ep + b->S) & 1;
+      if (b->adaptive) b->lc = 1 - b->lc;
+    }
+    CK(cudaEventRecord(e1, b->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    const double per = ms / trial_steps;
+    if (ms_out) ms_out[c] = per;
+    if (per < best) {
+      best = per;
+      best_block = cand[c];
+    }
+    CK(cudaMemcpyAsync(b->w[0], save, b->sz_state, cudaMemcpyDeviceToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->t, save_t, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, b->stream));
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaStreamSynchronize(b->stream));
+  cudaFree(save);
+  cudaFree(save_t);
+  b->ep = ep0;
+  b->lc = lc0;
+  b->evaluated = false;   // re-evaluate the restored state
+  (void)ev0;
+  if ((s = build_items(b, best_block)) != DG_OK) return s;
+  if (block_out) *block_out = best_block;
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -124,6 +124,41 @@ __device__ __forceinline__ void tprod(const R* a, const R* b, R* out) {
   });
 }
 
+// The four projected momentum products Pi(U u), Pi(U v), Pi(V u), Pi(V v)
+// onto P^{p-1}, sharing the rows (T_n u)_i = sum_m T[n][i][m] u_m and
+// (T_n v)_i between the U and V contractions.
+template <int P, class R>
+__device__ __forceinline__ void momentum_products(const R* U, const R* V, const R* u, const R* v, R* Puu, R* Puv,
+                                                  R* Pvu, R* Pvv) {
+  using Tb = RefTables<P>;
+  constexpr int K = Tb::K, K1 = Dims<P>::K1;
+  sfor<0, K1>([&](auto n) {
+    R auu = R(0), auv = R(0), avu = R(0), avv = R(0);
+    sfor<0, K>([&](auto i) {
+      R ru = R(0), rv = R(0);
+      bool any = false;
+      sfor<0, K>([&](auto m) {
+        constexpr double t = Tb::T[CV(n)][CV(i)][CV(m)];
+        if constexpr (t != 0.0) {
+          ru = fma(R(t), u[CV(m)], ru);
+          rv = fma(R(t), v[CV(m)], rv);
+          any = true;
+        }
+      });
+      if (any) {
+        auu = fma(U[CV(i)], ru, auu);
+        avu = fma(V[CV(i)], ru, avu);
+        auv = fma(U[CV(i)], rv, auv);
+        avv = fma(V[CV(i)], rv, avv);
+      }
+    });
+    Puu[CV(n)] = auu;
+    Puv[CV(n)] = auv;
+    Pvu[CV(n)] = avu;
+    Pvv[CV(n)] = avv;
+  });
+}
+
 // sum_i S[r][a][i] f[i]  (S vanishes for i beyond P^{p-1})
 template <int P, int r, int a, class R>
 __device__ __forceinline__ R sdot_row(const R* f) {
@@ -271,7 +306,7 @@ struct StageParams {
   const Real* w0;     // [3][K][E] RK base state (read when alpha != 0)
   Real* wout;         // [3][K][E] (may alias w0: each thread reads its own
                       // element of w0 before writing it)
-  double alpha, beta;
+  double alpha, beta;  // SSP stage w' = alpha w0 + beta (w + dt R); alpha + beta = 1
   // evaluation buffers of w (read) and of wout (written)
   const Real* vs;     // [3][K][E]
   const Real* rec;    // [3 edges][NREC][E]
@@ -289,6 +324,8 @@ struct StageParams {
   double* lam_clear;  // slot zeroed by thread 0 (or null)
   double* t;          // time, advanced by dt by thread 0 (or null)
   double inv_det;     // 1 / |det B| (uniform mesh)
+  double det;         // |det B|
+  double tau_bf, f_c; // bottom friction and Coriolis (Eq. (2)); both 0 = off
   unsigned* err;      // error word (ERRF_* bits)
   Real* rhs_out;      // mode MODE_RHS output [3][K][E]
 };
@@ -317,37 +354,66 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
   const long long E = sp.m.E;
   Real nx, ny, len;
   edge_geom(sp.m, t, NN, nx, ny, len);
-  Real tx[P1], tU[P1], tV[P1], tu[P1], tv[P1], th[P1];
+  const Real hl = Real(0.5) * len;
+  const Real hg = Real(0.5) * sp.g;
+  Real tx[P1], tU[P1], tV[P1], th[P1], xe[P1], Hs[P1];
   trace<NN, P>(xi, tx);
   trace<NN, P>(U, tU);
   trace<NN, P>(V, tV);
-  trace<NN, P>(u, tu);
-  trace<NN, P>(v, tv);
-  Real un[P1], qn[P1], xe[P1], Hs[P1];
   sfor<0, P1>([&](auto j) {
     constexpr int jj = CV(j);
     th[jj] = sp.hbt[(NN * P1 + jj) * E + e];
-    un[jj] = fma(nx, tu[jj], ny * tv[jj]);
-    qn[jj] = fma(nx, tU[jj], ny * tV[jj]);
     xe[jj] = fma(Real(2), th[jj], tx[jj]);
     Hs[jj] = tx[jj] + th[jj];
   });
-  Real Pp[P1], PU[P1], PV[P1];
+  Real Pp[P1], PU[P1], PV[P1], un[P1];
   lprod<P>(tx, xe, Pp);
-  lprod<P>(tU, un, PU);
-  lprod<P>(tV, un, PV);
-  const Real hl = Real(0.5) * len;
-  const Real hg = Real(0.5) * sp.g;
   Real* rb = sp.rec_out + (long long)NN * NREC * E + e;
+  if constexpr (NN == 0) {
+    // diagonal: n = s (hy, hx) / diag
+    Real tu[P1], tv[P1], qn[P1];
+    trace<NN, P>(u, tu);
+    trace<NN, P>(v, tv);
+    sfor<0, P1>([&](auto j) {
+      constexpr int jj = CV(j);
+      un[jj] = fma(nx, tu[jj], ny * tv[jj]);
+      qn[jj] = fma(nx, tU[jj], ny * tV[jj]);
+    });
+    lprod<P>(tU, un, PU);
+    lprod<P>(tV, un, PV);
+    sfor<0, P1>([&](auto j) {
+      constexpr int jj = CV(j);
+      rb[(0 * P1 + jj) * E] = hl * qn[jj];
+      rb[(1 * P1 + jj) * E] = hl * fma(hg * nx, Pp[jj], PU[jj]);
+      rb[(2 * P1 + jj) * E] = hl * fma(hg * ny, Pp[jj], PV[jj]);
+    });
+  } else {
+    // axis-aligned: n = -s e_x (edge 1) or -s e_y (edge 2), s = +1 lower,
+    // -1 upper; u.n = -s u_1 (or -s v), and the sign folds into the scale
+    const Real sh = (t ? Real(1) : Real(-1)) * hl;   // -s |E|/2
+    trace<NN, P>(NN == 1 ? u : v, un);               // u.n up to the sign -s
+    lprod<P>(tU, un, PU);
+    lprod<P>(tV, un, PV);
+    sfor<0, P1>([&](auto j) {
+      constexpr int jj = CV(j);
+      if constexpr (NN == 1) {
+        rb[(0 * P1 + jj) * E] = sh * tU[jj];
+        rb[(1 * P1 + jj) * E] = sh * fma(hg, Pp[jj], PU[jj]);
+        rb[(2 * P1 + jj) * E] = sh * PV[jj];
+      } else {
+        rb[(0 * P1 + jj) * E] = sh * tV[jj];
+        rb[(1 * P1 + jj) * E] = sh * PU[jj];
+        rb[(2 * P1 + jj) * E] = sh * fma(hg, Pp[jj], PV[jj]);
+      }
+    });
+  }
   sfor<0, P1>([&](auto j) {
     constexpr int jj = CV(j);
-    rb[(0 * P1 + jj) * E] = hl * qn[jj];
-    rb[(1 * P1 + jj) * E] = hl * fma(hg * nx, Pp[jj], PU[jj]);
-    rb[(2 * P1 + jj) * E] = hl * fma(hg * ny, Pp[jj], PV[jj]);
     rb[(3 * P1 + jj) * E] = tx[jj];
     rb[(4 * P1 + jj) * E] = tU[jj];
     rb[(5 * P1 + jj) * E] = tV[jj];
   });
+  // wave speed of this side at s = 0, 1/2, 1 (|u.n| is sign-free)
   const Real h0 = edge_point<P, 0>(Hs), h1 = edge_point<P, 1>(Hs), h2 = edge_point<P, 2>(Hs);
   const Real u0 = edge_point<P, 0>(un), u1 = edge_point<P, 1>(un), u2 = edge_point<P, 2>(un);
   if (!(h0 > Real(0)) || !(h1 > Real(0)) || !(h2 > Real(0))) err |= ERRF_DRY;
@@ -378,10 +444,7 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
   Real xe[K];
   sfor<0, K>([&](auto i) { xe[CV(i)] = fma(Real(2), hb[CV(i)], xi[CV(i)]); });
   Real Puu[K1], Puv[K1], Pvu[K1], Pvv[K1], Pxx[K1];
-  tprod<P, K1, K>(U, u, Puu);
-  tprod<P, K1, K>(U, v, Puv);
-  tprod<P, K1, K>(V, u, Pvu);
-  tprod<P, K1, K>(V, v, Pvv);
+  momentum_products<P>(U, V, u, v, Puu, Puv, Pvu, Pvv);
   tprod<P, K1, K>(xi, xe, Pxx);
   const Real hg = Real(0.5) * sp.g;
   Real FxU[K1], FyV[K1];
@@ -409,6 +472,12 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
     Real v2 = G11 * sdot_row<P, 0, aa>(Pvu) + G22 * sdot_row<P, 1, aa>(FyV);
     v1 = fma(sp.g, Sx[aa], v1);
     v2 = fma(sp.g, Sy[aa], v2);
+    if (sp.tau_bf != 0.0 || sp.f_c != 0.0) {
+      // (-tau_bf q + f_c (V, -U), phi_a) = |det B| (-tau_bf U_a + f_c V_a, ...)
+      const Real tq = Real(-sp.tau_bf * sp.det), fq = Real(sp.f_c * sp.det);
+      v1 = fma(tq, U[aa], fma(fq, V[aa], v1));
+      v2 = fma(tq, V[aa], fma(-fq, U[aa], v2));
+    }
     sp.vs_out[(0 * K + aa) * E + e] = v0;
     sp.vs_out[(1 * K + aa) * E + e] = v1;
     sp.vs_out[(2 * K + aa) * E + e] = v2;
@@ -478,13 +547,84 @@ __device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long
 template <class Real>
 __device__ __forceinline__ bool finite(Real x) { return isfinite(x); }
 
+// Work of one element in one launch: MODE_STAGE = flux, lift, RK update and
+// evaluation of the new state; MODE_EVAL = evaluation only; MODE_RHS = flux
+// and lift of an evaluated state, written as d_t c.  Returns the element's
+// wave speed (0 unless sp.lam_next is set) through lam_e.
+template <int P, class Real, class PR, int MODE>
+__device__ __forceinline__ void stage_element(const StageParams<Real>& sp, long long e, double dt, double& lam_e,
+                                              unsigned& err) {
+  using D = Dims<P>;
+  constexpr int K = D::K;
+  const long long E = sp.m.E;
+  const int t = (int)(e & 1);
+  Real w[3][K];
+  sfor<0, 3>([&](auto f) {
+    sfor<0, K>([&](auto i) { w[CV(f)][CV(i)] = sp.w[(CV(f) * K + CV(i)) * E + e]; });
+  });
+  if constexpr (MODE == MODE_EVAL) {
+    lam_e = evaluate<P, Real, PR>(sp, e, t, w[0], w[1], w[2], err);
+  } else {
+    Real res[3][K];
+    sfor<0, 3>([&](auto f) {
+      sfor<0, K>([&](auto i) { res[CV(f)][CV(i)] = sp.vs[(CV(f) * K + CV(i)) * E + e]; });
+    });
+    edge_flux_lift<0, P>(sp, e, t, res);
+    edge_flux_lift<1, P>(sp, e, t, res);
+    edge_flux_lift<2, P>(sp, e, t, res);
+    if constexpr (MODE == MODE_RHS) {
+      const Real idet = Real(sp.inv_det);
+      sfor<0, 3>([&](auto f) {
+        sfor<0, K>([&](auto i) { sp.rhs_out[(CV(f) * K + CV(i)) * E + e] = res[CV(f)][CV(i)] * idet; });
+      });
+    } else {
+      // w' = alpha w0 + beta (w + dt R),  R = res / |det B|, alpha + beta = 1,
+      // evaluated as w0 + beta ((w - w0) + dt R): a constant state stays
+      // exactly constant and the result is rounded once (alpha and beta
+      // themselves are never rounded to the working precision)
+      const Real b = Real(sp.beta), c = Real(dt * sp.inv_det);
+      bool fin = true;
+      sfor<0, 3>([&](auto f) {
+        sfor<0, K>([&](auto i) {
+          const long long idx = (CV(f) * K + CV(i)) * E + e;
+          Real x;
+          if (sp.alpha != 0.0) {
+            const Real base = sp.w0[idx];
+            x = fma(b, fma(c, res[CV(f)][CV(i)], w[CV(f)][CV(i)] - base), base);
+          } else {
+            x = fma(c, res[CV(f)][CV(i)], w[CV(f)][CV(i)]);
+          }
+          fin = fin && finite(x);
+          w[CV(f)][CV(i)] = x;
+          sp.wout[idx] = x;
+        });
+      });
+      if (!fin) err |= ERRF_NONFINITE;
+      lam_e = evaluate<P, Real, PR>(sp, e, t, w[0], w[1], w[2], err);
+    }
+  }
+}
+
+// maximum of v over the block, valid in thread 0 (all threads must call)
+__device__ __forceinline__ double block_max(double v) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
 // One launch per RK stage (MODE_STAGE), per initial evaluation (MODE_EVAL) or
 // per right-hand side (MODE_RHS).  One thread per element.
 template <int P, class Real, class PR, int MODE>
 __global__ void __launch_bounds__(128) stage_kernel(const StageParams<Real> sp) {
-  using D = Dims<P>;
-  constexpr int K = D::K;
-  const long long E = sp.m.E;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double lam_e = 0.0;
   unsigned err = 0;
@@ -492,62 +632,10 @@ __global__ void __launch_bounds__(128) stage_kernel(const StageParams<Real> sp) 
   if constexpr (MODE == MODE_STAGE) {
     dt = sp.dt_fixed > 0.0 ? sp.dt_fixed : sp.cfl_num / sp.lam[0];
   }
-  if (e < E) {
-    const int t = (int)(e & 1);
-    Real w[3][K];
-    sfor<0, 3>([&](auto f) {
-      sfor<0, K>([&](auto i) { w[CV(f)][CV(i)] = sp.w[(CV(f) * K + CV(i)) * E + e]; });
-    });
-    if constexpr (MODE == MODE_EVAL) {
-      lam_e = evaluate<P, Real, PR>(sp, e, t, w[0], w[1], w[2], err);
-    } else {
-      Real res[3][K];
-      sfor<0, 3>([&](auto f) {
-        sfor<0, K>([&](auto i) { res[CV(f)][CV(i)] = sp.vs[(CV(f) * K + CV(i)) * E + e]; });
-      });
-      edge_flux_lift<0, P>(sp, e, t, res);
-      edge_flux_lift<1, P>(sp, e, t, res);
-      edge_flux_lift<2, P>(sp, e, t, res);
-      if constexpr (MODE == MODE_RHS) {
-        const Real idet = Real(sp.inv_det);
-        sfor<0, 3>([&](auto f) {
-          sfor<0, K>([&](auto i) {
-            sp.rhs_out[(CV(f) * K + CV(i)) * E + e] = res[CV(f)][CV(i)] * idet;
-          });
-        });
-      } else {
-        // w' = alpha w0 + beta (w + dt R),  R = res / |det B|
-        const Real a = Real(sp.alpha), b = Real(sp.beta), c = Real(sp.beta * dt * sp.inv_det);
-        bool fin = true;
-        sfor<0, 3>([&](auto f) {
-          sfor<0, K>([&](auto i) {
-            const long long idx = (CV(f) * K + CV(i)) * E + e;
-            Real x = fma(c, res[CV(f)][CV(i)], b * w[CV(f)][CV(i)]);
-            if (sp.alpha != 0.0) x = fma(a, sp.w0[idx], x);
-            fin = fin && finite(x);
-            w[CV(f)][CV(i)] = x;
-            sp.wout[idx] = x;
-          });
-        });
-        if (!fin) err |= ERRF_NONFINITE;
-        lam_e = evaluate<P, Real, PR>(sp, e, t, w[0], w[1], w[2], err);
-      }
-    }
-  }
-  // block reductions: wave-speed maximum and error bits
+  if (e < sp.m.E) stage_element<P, Real, PR, MODE>(sp, e, dt, lam_e, err);
   if (sp.lam_next) {
-    double l = lam_e;
-    for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
-    __shared__ double red[32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = l;
-    __syncthreads();
-    if (wid == 0) {
-      const int nw = (blockDim.x + 31) >> 5;
-      l = lane < nw ? red[lane] : 0.0;
-      for (int o = 16; o > 0; o >>= 1) l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
-      if (lane == 0) atomic_max_nonneg(sp.lam_next, l);
-    }
+    const double l = block_max(lam_e);
+    if (threadIdx.x == 0) atomic_max_nonneg(sp.lam_next, l);
   }
   if (err) atomicOr(sp.err, err);
   if (blockIdx.x == 0 && threadIdx.x == 0) {

@@ -108,6 +108,9 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   sp.hbt = reinterpret_cast<const Real*>(b + o_hbt);
   sp.ghb = reinterpret_cast<const Real*>(b + o_ghb);
   sp.inv_det = 1.0 / (hx * hy);
+  sp.det = hx * hy;
+  sp.tau_bf = cfg->tau_bf;
+  sp.f_c = cfg->f_c;
   sp.err = err;
   sp.w = static_cast<const Real*>(d_in);
   sp.vs_out = reinterpret_cast<Real*>(b + o_vs);

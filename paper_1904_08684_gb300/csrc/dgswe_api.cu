@@ -73,6 +73,7 @@ dg_status validate(const dg_config* c) {
   if (c->bc < 0 || c->bc > 2 || c->precision < 0 || c->precision > 1) return DG_ERR_ARG;
   if (c->proj_precision < 0 || c->proj_precision > 1) return DG_ERR_ARG;
   if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
+  if (!(c->tau_bf >= 0.0) || !std::isfinite(c->tau_bf) || !std::isfinite(c->f_c)) return DG_ERR_ARG;
   // the stage kernels are compiled for at most 128 threads per block
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 128 || c->block_size % 32)) return DG_ERR_ARG;
   if (c->bc == DG_BC_PERIODIC && (c->nx < 2 || c->ny < 2)) return DG_ERR_ARG;
@@ -102,6 +103,9 @@ StageParams<Real> base_params(const dg_ctx* c) {
   sp.dt_fixed = c->cfg.dt > 0.0 ? c->cfg.dt : 0.0;
   sp.cfl_num = c->cfl_num;
   sp.inv_det = c->inv_det;
+  sp.det = c->det;
+  sp.tau_bf = c->cfg.tau_bf;
+  sp.f_c = c->cfg.f_c;
   sp.err = c->err;
   return sp;
 }

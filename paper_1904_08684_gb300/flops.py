@@ -13,6 +13,7 @@ re-reads per-element volume integrals (3K) and edge side records
 (3 x (6(p+1)+1)); that extra traffic is reported separately.
 """
 import functools
+import hashlib
 import os
 import sys
 
@@ -30,6 +31,29 @@ def _tables(p):
     leg = gt.shifted_legendre(gt.PMAX)
     K, P1, T, S, R, Lam, Lpt = gt.tables_for(p, basis, leg)
     return K, P1, T, S, R, Lam, Lpt
+
+
+# Algorithmic work per element and RK stage used for the roofline: FP64 FMAs
+# of the velocity solve and FMAs of everything else, counted from the tensor
+# nonzeros (nnz T/2 + K^3/6 + 2K^2 for the solve; products, contractions,
+# traces, fluxes and lifts for the rest).
+SURVEY_FMA = {1: (28, 478), 2: (160, 1498), 3: (564, 4143), 4: (1588, 10344)}
+
+
+def algorithmic_flops(p):
+    """flops per element and stage (2 per FMA) of the reference count"""
+    a, b = SURVEY_FMA[p]
+    return 2 * (a + b)
+
+
+def source_hash():
+    """hash of the kernel sources: measured traffic is valid only for it"""
+    h = hashlib.sha1()
+    for name in sorted(os.listdir(_CSRC)):
+        if name.endswith((".cu", ".cuh", ".py")):
+            with open(os.path.join(_CSRC, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
 
 
 def _nz(x):

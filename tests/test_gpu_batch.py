@@ -1,0 +1,113 @@
+"""Batched instances (one persistent launch per RK stage) against separate
+single-instance contexts (bit-identical: the element code is shared) and,
+for one instance, against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from paper_1904_08684_gb300 import binding as B
+from paper_1904_08684_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# (nx, ny, p, bc): uneven sizes and orders, ragged work items
+SPECS = [(7, 5, 3, "periodic"), (12, 9, 1, "reflective"), (5, 6, 2, "periodic"), (11, 13, 2, "reflective"),
+         (9, 4, 1, "periodic"), (6, 6, 3, "reflective")]
+
+
+def _instance(k, nx, ny, p, bc, precision):
+    r = I.uniform(100 + k, 6)
+    wl = I.Workload("b%d" % k, nx, ny, p, bc, 3, 0.2, 0, precision,
+                    hb=I.fourier_bathymetry(12.0, [1.5 * r[0], 1.0 * r[1]], [1, 0], [1, 2], [0, 1]),
+                    xi0=I.gaussian_sum([0.02 + 0.05 * r[2]], [0.1], [r[3]], [r[4]], periodic=(bc == "periodic")))
+    cfg = B.make_config(nx, ny, p, bc=bc, precision=precision, rk_order=3, cfl=0.2 + 0.1 * r[5])
+    Q, E, K = B.dg_proj_num_nodes(p), wl.E, wl.K
+    xy = torch.empty((2, Q, E), dtype=torch.float64, device="cuda")
+    B.dg_proj_nodes(cfg, xy)
+    fields = []
+    for f in (wl.hb, wl.xi0, lambda x, y: 0.1 * torch.sin(2 * np.pi * x), lambda x, y: 0.0 * x - 0.05):
+        c = torch.empty((K, E), dtype=torch.float64, device="cuda")
+        B.dg_project(cfg, f(xy[0], xy[1]).contiguous(), c)
+        fields.append(c)
+    torch.cuda.synchronize()
+    return cfg, fields, E, K
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    B.load()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_equals_single_contexts(precision):
+    inst = [_instance(k, *s, precision) for k, s in enumerate(SPECS)]
+    steps = 15
+    ref = []
+    for cfg, f, E, K in inst:
+        ctx = B.dg_init_device(cfg, *f)
+        t = B.dg_run(ctx, steps)
+        ref.append((B.dg_get_state(ctx, E, K), t))
+        B.dg_destroy(ctx)
+    b = B.dg_batch_init([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
+                        [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
+    try:
+        assert B.dg_batch_dofs(b) == sum(3 * K * E for _, _, E, K in inst)
+        t = B.dg_batch_run(b, steps)
+        for i, (cfg, f, E, K) in enumerate(inst):
+            st = B.dg_batch_get_state(b, i, E, K)
+            assert t[i] == ref[i][1]
+            for a, r in zip(st, ref[i][0]):
+                assert np.array_equal(a, r), (i, np.abs(a - r).max())
+    finally:
+        B.dg_batch_destroy(b)
+
+
+def test_batch_autotune_keeps_state():
+    inst = [_instance(k, *s, "fp32") for k, s in enumerate(SPECS)]
+    args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
+            [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
+    b1 = B.dg_batch_init(*args)
+    b2 = B.dg_batch_init(*args)
+    try:
+        t1 = B.dg_batch_run(b1, 5)
+        blk, ms = B.dg_batch_autotune(b2, 2)
+        assert blk in (32, 64, 96, 128) and (ms > 0).all()
+        t2 = B.dg_batch_run(b2, 5)
+        assert np.array_equal(t1, t2)
+        for i, (_, _, E, K) in enumerate(inst):
+            for a, r in zip(B.dg_batch_get_state(b2, i, E, K), B.dg_batch_get_state(b1, i, E, K)):
+                assert np.array_equal(a, r)
+        for blk in (32, 96):
+            B.dg_batch_set_block(b1, blk)
+            B.dg_batch_run(b1, 1)
+    finally:
+        B.dg_batch_destroy(b1)
+        B.dg_batch_destroy(b2)
+
+
+def test_batch_instance_matches_oracle(oracle_mod):
+    """one FP64 batch instance against the oracle (20 steps, <= 1e-12)."""
+    nx, ny, p, bc = SPECS[3]
+    o = oracle_mod.Oracle(nx, ny, p, bc=bc, rk_order=3, cfl=0.25)
+    wl = I.waves_p2_512(n=nx, p=p, ngauss=2)
+    hb = o.project_hb(wl.hb)
+    xi = o.project(wl.xi0)
+    U = o.project(lambda x, y: 0.2 + 0.1 * np.cos(2 * np.pi * y))
+    V = np.zeros_like(xi)
+    xr, Ur, Vr, tr, _ = o.run(hb, xi, U, V, 20)
+    cfg = B.make_config(nx, ny, p, bc=bc, precision="fp64", rk_order=3, cfl=0.25)
+    dev = [torch.tensor(a.T.copy(), dtype=torch.float64, device="cuda").contiguous() for a in (hb, xi, U, V)]
+    other = _instance(0, *SPECS[0], "fp64")
+    b = B.dg_batch_init([other[0], cfg], [other[1][0], dev[0]], [other[1][1], dev[1]],
+                        [other[1][2], dev[2]], [other[1][3], dev[3]])
+    try:
+        t = B.dg_batch_run(b, 20)
+        xg, Ug, Vg = B.dg_batch_get_state(b, 1, o.E, o.K)
+    finally:
+        B.dg_batch_destroy(b)
+    assert abs(t[1] - tr) <= 1e-13 * tr
+    for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr)):
+        assert np.linalg.norm(g_ - r_) <= 1e-12 * np.linalg.norm(r_)

@@ -72,7 +72,7 @@ def _gpu_rhs(cfg, hb, xi, U, V, dtype=torch.float64):
 
 
 # ------------------------------------------------------------------ RHS
-@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("bc", ["periodic", "reflective"])
 def test_rhs_matches_oracle_fp64(oracle_mod, p, bc):
     """13 x 11 quads = 286 triangles: several 128-thread blocks and a ragged tail."""
@@ -86,6 +86,22 @@ def test_rhs_matches_oracle_fp64(oracle_mod, p, bc):
     for f in range(3):
         scale = np.abs(ref[f]).max()
         assert np.abs(got[f] - ref[f]).max() <= 1e-13 * scale, (f, np.abs(got[f] - ref[f]).max() / scale)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("proj", ["fp64", "fp32"])
+def test_rhs_fp32_state(oracle_mod, p, proj):
+    """FP32 state and contractions (velocity solve in FP64 or FP32): the RHS
+    agrees with the FP64 oracle to FP32 round-off amplified by the
+    Lax-Friedrichs jump term (|jump| ~ eps |w|, times lambda / h)."""
+    wl = I.waves_p2_512(n=13, p=p, ngauss=3)
+    wl.ny = 11
+    o = oracle_mod.Oracle(wl.nx, wl.ny, p, bc="periodic")
+    hb, xi, U, V = _state(o, wl)
+    ref = o.rhs(hb, xi, U, V)
+    got = _gpu_rhs(_cfg(wl, precision="fp32", proj_precision=proj), hb, xi, U, V, dtype=torch.float32)
+    for f in range(3):
+        assert _relL2(got[f], ref[f]) <= 2e-5, (f, _relL2(got[f], ref[f]))
 
 
 def test_rhs_nonsquare_domain(oracle_mod):
@@ -282,3 +298,15 @@ def test_dry_state_is_reported():
         assert xg.shape == (E, K)
     finally:
         B.dg_destroy(ctx)
+
+
+def test_rhs_friction_coriolis(oracle_mod):
+    """bottom friction tau_bf and Coriolis f_c of Eq. (2) (source r of Eq. (5))"""
+    wl = I.waves_p2_512(n=9, p=2, ngauss=2)
+    wl.ny = 7
+    for bc in ("periodic", "reflective"):
+        o = oracle_mod.Oracle(9, 7, 2, bc=bc, tau_bf=0.03, f_c=1.2e-4 * 1000)
+        hb, xi, U, V = _state(o, wl, U0=0.3, V0=-0.2)
+        ref = o.rhs(hb, xi, U, V)
+        got = _gpu_rhs(_cfg(wl, bc=bc, tau_bf=0.03, f_c=0.12), hb, xi, U, V)
+        assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()

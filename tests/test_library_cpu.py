@@ -53,9 +53,9 @@ def test_counts_and_status_strings(lib):
 
 def test_config_struct_layout(lib):
     from paper_1904_08684_gb300 import binding as B
-    # int,int | 4 double | ptr | int(+pad) | double | 3 int(+pad) | 2 double | 2 int
-    assert ctypes.sizeof(B.dg_config) == 104
-    assert B.dg_config.g.offset == 56 and B.dg_config.cfl.offset == 80
+    # int,int | 4 double | ptr | int(+pad) | double | 3 int(+pad) | 2 double | 2 int | 2 double
+    assert ctypes.sizeof(B.dg_config) == 120
+    assert B.dg_config.g.offset == 56 and B.dg_config.cfl.offset == 80 and B.dg_config.tau_bf.offset == 104
 
 
 @pytest.mark.parametrize("bad", [dict(nx=0), dict(p=5), dict(rk_order=4), dict(Lx=-1.0),
@@ -84,3 +84,21 @@ def test_unsupported_configs(lib):
         with pytest.raises(B.DGError) as ei:
             B.dg_init(cfg, z, z, z, z)
         assert ei.value.status == B.DG_ERR_UNSUPPORTED
+
+
+def test_batch_rejects_mixed_or_unsupported_without_gpu(lib):
+    """Batch validation runs before any CUDA call."""
+    from paper_1904_08684_gb300 import binding as B
+    a = B.make_config(4, 4, 2, precision="fp64")
+    b = B.make_config(4, 4, 1, precision="fp32")
+    c = B.make_config(4, 4, 4)
+    one = [1, 1]
+    with pytest.raises(B.DGError) as ei:
+        B.dg_batch_init([a, b], one, one, one, one)
+    assert ei.value.status == B.DG_ERR_ARG
+    with pytest.raises(B.DGError) as ei:
+        B.dg_batch_init([c], [1], [1], [1], [1])
+    assert ei.value.status == B.DG_ERR_UNSUPPORTED
+    with pytest.raises(B.DGError) as ei:
+        B.dg_batch_init([], [], [], [], [])
+    assert ei.value.status == B.DG_ERR_ARG
