@@ -67,14 +67,29 @@ typedef enum {
 typedef enum { DG_BC_PERIODIC = 0, DG_BC_REFLECTIVE = 1, DG_BC_DIRICHLET = 2 } dg_bc;
 typedef enum { DG_PREC_FP64 = 0, DG_PREC_FP32_MIXED = 1 } dg_precision;
 typedef enum { DG_PROJ_FP64 = 0, DG_PROJ_FP32 = 1 } dg_proj_precision;
+/* §3.1 convergence test of the paper: xi = 2.3 - 0.4 S, U = 0.6 + 0.04 S,
+ * V = 0.3 + 0.04 S, S = sin(pi (x + y + 0.2 t) / 600), on the bathymetry
+ * h_b = 1 + x/1000 + 2 y/1000 (which the caller projects), with the body force
+ * F of Eq. (2) that makes it exact (tau_bf = f_c = 0).  The force enters the
+ * volume term through the reference scheme's Gauss rule
+ * (ceil((3p+2)/2)+1 points per direction, collapsed), the boundary data the
+ * edge term through ceil((3p+1)/2)+1 Gauss points. */
+typedef enum { DG_FORCING_NONE = 0, DG_FORCING_MANUFACTURED = 1 } dg_forcing;
 
 typedef struct {
   int nx, ny;              /* quads; E = 2 nx ny triangles                      */
   double x0, y0, Lx, Ly;   /* domain                                            */
-  const double* vertex_xy; /* must be NULL: perturbed meshes are not built yet  */
+  const double* vertex_xy; /* NULL: uniform mesh; else (nx+1)(ny+1) vertices
+                              (x, y), row j major (vertex (i, j) at
+                              [2 (j (nx+1) + i)]): a general quad-split mesh
+                              with the same topology (e.g. the randomly
+                              perturbed meshes of §3.1); walls or Dirichlet
+                              only, every triangle counter-clockwise; the
+                              array is read by dg_init and not kept           */
   int p;                   /* polynomial order, 1..4 (0 returns UNSUPPORTED)    */
   double g;                /* gravitational acceleration                        */
-  int bc;                  /* dg_bc; DG_BC_DIRICHLET returns UNSUPPORTED        */
+  int bc;                  /* dg_bc; DG_BC_DIRICHLET needs DG_FORCING_MANUFACTURED
+                              (the only boundary data source)                 */
   int precision;           /* dg_precision                                      */
   int rk_order;            /* 1, 2 or 3 (SSP Runge-Kutta)                       */
   double cfl;              /* used when dt <= 0                                 */
@@ -86,6 +101,10 @@ typedef struct {
                               32, 64, 96 or 128                               */
   double tau_bf;           /* bottom friction coefficient of Eq. (2) (>= 0)    */
   double f_c;              /* Coriolis coefficient of Eq. (2)                  */
+  int forcing;             /* dg_forcing: DG_FORCING_MANUFACTURED adds the
+                              body force of the §3.1 analytic solution and,
+                              with DG_BC_DIRICHLET, uses that solution as the
+                              boundary data                                    */
 } dg_config;
 
 typedef struct dg_ctx dg_ctx;
@@ -156,7 +175,8 @@ dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, voi
  * fixed at start-up, or hosts that forbid libraries from growing the device
  * heap -- and therefore cannot create a dg_ctx (dg_init allocates).
  *   cfg:        mesh, order, boundary, precision as for dg_init (p = 1..4,
- *               periodic or reflective walls); dt, cfl, rk_order are ignored.
+ *               uniform mesh, periodic or reflective walls, no forcing);
+ *               dt, cfl, rk_order are ignored.
  *   d_hb:       device FP64 SoA [K][E] bathymetry coefficients (input).
  *   d_state_in: device SoA [3][K][E] state in cfg's precision (input).
  *   d_rhs_out:  device SoA [3][K][E] (output), must not overlap d_state_in.
@@ -164,14 +184,15 @@ dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, voi
  * Intermediates live in one fixed 32 MiB array inside the library's device
  * image, reserved on every GPU that loads the library until the process
  * exits.  A mesh needs about (K + 3(p+1) + p(p+1) + 3K + 3(6p+7)) words per
- * triangle (8 bytes FP64, 4 bytes FP32, each block rounded up to 256 bytes);
- * meshes that do not fit are rejected with DG_ERR_ARG before any GPU work
- * (about 43,000 triangles at p = 2 in FP64).  The first call on a device looks
+ * triangle, plus 2K^2 in FP64 (8 bytes FP64, 4 bytes FP32, each block rounded
+ * up to 256 bytes); meshes that do not fit are rejected with DG_ERR_ARG before
+ * any GPU work (about 24,000 triangles at p = 2 in FP64).  The first call on a device looks
  * up the array's device address once (cudaGetSymbolAddress); make that first
  * call before any stream capture.  Every call shares the array, which keeps
  * the previous call's contents (the error word is cleared per call); calls
  * whose GPU work overlaps race and give wrong results.
- * Errors: DG_ERR_ARG (invalid or too large), DG_ERR_CUDA. */
+ * Errors: DG_ERR_ARG (invalid or too large), DG_ERR_UNSUPPORTED (forcing),
+ * DG_ERR_CUDA. */
 dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_state_in, void* d_rhs_out,
                          void* stream);
 
@@ -184,7 +205,8 @@ dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_s
  * element code), so results equal those of separate dg_init contexts. */
 typedef struct dg_batch dg_batch;
 
-/* n instances; cfgs[i] as for dg_init with p = 1..3 and nx, ny >= 2.  All
+/* n instances; cfgs[i] as for dg_init with p = 1..3, nx, ny >= 2, uniform
+ * meshes without forcing (else DG_ERR_UNSUPPORTED).  All
  * instances share precision, proj_precision, rk_order and fixed-vs-CFL time
  * stepping (else DG_ERR_ARG).  d_hb[i], d_xi[i], d_qx[i], d_qy[i]: DEVICE
  * FP64 SoA [K_i][E_i] arrays (copied).  Errors: DG_ERR_ARG,

@@ -44,17 +44,25 @@ class dg_config(ctypes.Structure):
                 ("bc", ctypes.c_int), ("precision", ctypes.c_int), ("rk_order", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("proj_precision", ctypes.c_int), ("block_size", ctypes.c_int),
-                ("tau_bf", ctypes.c_double), ("f_c", ctypes.c_double)]
+                ("tau_bf", ctypes.c_double), ("f_c", ctypes.c_double), ("forcing", ctypes.c_int)]
 
 
 def make_config(nx, ny, p, bc="periodic", precision="fp64", rk_order=3, cfl=0.2, dt=0.0, g=9.81,
-                x0=0.0, y0=0.0, Lx=1.0, Ly=1.0, proj_precision="fp64", block_size=0, tau_bf=0.0, f_c=0.0):
-    return dg_config(nx, ny, x0, y0, Lx, Ly, None, p, g,
+                x0=0.0, y0=0.0, Lx=1.0, Ly=1.0, proj_precision="fp64", block_size=0, tau_bf=0.0, f_c=0.0,
+                vertex_xy=None, forcing=0):
+    vxy = None
+    if vertex_xy is not None:
+        _keep = np.ascontiguousarray(vertex_xy, dtype=np.float64).ravel()
+        vxy = _keep.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    cfg = dg_config(nx, ny, x0, y0, Lx, Ly, vxy, p, g,
                      BC[bc] if isinstance(bc, str) else int(bc),
                      PREC[precision] if isinstance(precision, str) else int(precision),
                      rk_order, cfl, dt,
                      DG_PROJ_FP32 if proj_precision == "fp32" else DG_PROJ_FP64, block_size,
-                     float(tau_bf), float(f_c))
+                     float(tau_bf), float(f_c), int(forcing))
+    if vertex_xy is not None:
+        cfg._vertex_keep = _keep   # keep the vertex array alive with the struct
+    return cfg
 
 
 _lib = None

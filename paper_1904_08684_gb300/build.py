@@ -18,8 +18,9 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libdgswe.so")
 
-UNITS = ["dg_fp64.cu", "dg_fp32p64.cu", "dg_fp32p32.cu", "dgswe_api.cu", "dg_project.cu", "dg_noalloc.cu",
-         "dg_batch_fp64.cu", "dg_batch_fp32p64.cu", "dg_batch_fp32p32.cu", "dg_batch_api.cu"]
+UNITS = ["dg_fp64.cu", "dg_fp64_gen.cu", "dg_fp32p64.cu", "dg_fp32p64_gen.cu", "dg_fp32p32.cu",
+         "dg_fp32p32_gen.cu", "dgswe_api.cu", "dg_project.cu", "dg_noalloc.cu", "dg_batch_fp64.cu",
+         "dg_batch_fp32p64.cu", "dg_batch_fp32p32.cu", "dg_batch_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"] + ARCH
 
@@ -63,7 +64,8 @@ def build_library(force=False, verbose=False):
     subprocess.check_call([sys.executable, os.path.join(CSRC, "gen_tables.py"),
                            os.path.join(BUILD, "dg_ref_tables.h")],
                           stdout=subprocess.DEVNULL)
-    with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
+    workers = max(1, min(len(UNITS), os.cpu_count() or 1))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         objs = list(ex.map(_compile, UNITS))
     tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.check_call([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs)

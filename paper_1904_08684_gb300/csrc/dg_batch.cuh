@@ -25,6 +25,7 @@ struct BatchInst {
   const void* hb;
   const void* hbt;
   const void* ghb;
+  const void* lin;     // FP64 batches: [2][K][K][E], else null
   double* lam;         // slot s of this instance at lam[s * n_inst]
   double* t;
   int p;
@@ -64,6 +65,7 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchArgs a) {
     sp.hb = static_cast<const Real*>(d.hb);
     sp.hbt = static_cast<const Real*>(d.hbt);
     sp.ghb = static_cast<const Real*>(d.ghb);
+    sp.lin = static_cast<const Real*>(d.lin);
     sp.inv_det = d.inv_det;
     sp.det = d.det;
     sp.tau_bf = d.tau_bf;
@@ -76,7 +78,14 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchArgs a) {
     sp.w0 = static_cast<const Real*>(d.w[0]);
     sp.rhs_out = nullptr;
     sp.lam_clear = nullptr;
-    sp.t = nullptr;
+    sp.forcing = 0;
+    sp.dirichlet = 0;
+    sp.t_now = nullptr;
+    sp.c_eval = 0.0;
+    sp.vq = nullptr;
+    sp.nqv = 0;
+    sp.eq = nullptr;
+    sp.nqe = 0;
     double* lam_target = nullptr;
     double dt = 0.0;
     if constexpr (MODE == MODE_EVAL) {
@@ -105,9 +114,9 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchArgs a) {
     unsigned err = 0;
     if (e < d.m.E) {
       switch (d.p) {
-        case 1: stage_element<1, Real, PR, MODE>(sp, e, dt, lam_e, err); break;
-        case 2: stage_element<2, Real, PR, MODE>(sp, e, dt, lam_e, err); break;
-        default: stage_element<3, Real, PR, MODE>(sp, e, dt, lam_e, err); break;
+        case 1: stage_element<1, Real, PR, MODE, 0>(sp, e, dt, lam_e, err); break;
+        case 2: stage_element<2, Real, PR, MODE, 0>(sp, e, dt, lam_e, err); break;
+        default: stage_element<3, Real, PR, MODE, 0>(sp, e, dt, lam_e, err); break;
       }
     }
     if (lam_target) {

@@ -38,7 +38,7 @@ struct HostInst {
   dg_config cfg;
   int p, K, K1, P1, NREC;
   long long E;
-  size_t o_state, o_rec, o_hb, o_hbt, o_ghb;  // byte offsets in the arenas
+  size_t o_state, o_rec, o_hb, o_hbt, o_ghb, o_lin;  // byte offsets in the arenas
 };
 
 }  // namespace
@@ -58,6 +58,7 @@ struct dg_batch {
   void* hb = nullptr;
   void* hbt = nullptr;
   void* ghb = nullptr;
+  void* lin = nullptr;          // FP64 batches only
   double* lam = nullptr;        // [2][n]
   double* t = nullptr;          // [n]
   unsigned* err = nullptr;
@@ -185,7 +186,7 @@ void free_batch(dg_batch* b) {
   if (!b) return;
   drop_graphs(b);
   void* bufs[] = {b->w[0], b->w[1], b->w[2], b->vs[0], b->vs[1], b->rec[0], b->rec[1], b->hb, b->hbt,
-                  b->ghb, b->lam, b->t, b->err, b->counters, b->d_inst, b->d_items};
+                  b->ghb, b->lin, b->lam, b->t, b->err, b->counters, b->d_inst, b->d_items};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -216,7 +217,7 @@ dg_status validate_one(const dg_config* c) {
   if (c->nx < 2 || c->ny < 2 || c->p < 1 || c->p > 3) return c->p > 3 ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
   if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
   if (c->rk_order < 1 || c->rk_order > 3 || c->bc < 0 || c->bc > 2) return DG_ERR_ARG;
-  if (c->bc == DG_BC_DIRICHLET || c->vertex_xy) return DG_ERR_UNSUPPORTED;
+  if (c->bc == DG_BC_DIRICHLET || c->vertex_xy || c->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
   if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
   if (2.0 * c->nx * (double)c->ny > 2.0e9) return DG_ERR_ARG;
   return DG_OK;
@@ -247,7 +248,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   b->S = cfgs[0].rk_order;
   b->adaptive = !(cfgs[0].dt > 0.0);
   b->stream = (cudaStream_t)stream;
-  size_t ost = 0, orec = 0, ohb = 0, ohbt = 0, oghb = 0;
+  size_t ost = 0, orec = 0, ohb = 0, ohbt = 0, oghb = 0, olin = 0;
   b->dofs = 0;
   for (int i = 0; i < n; ++i) {
     HostInst h;
@@ -263,11 +264,13 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     h.o_hb = ohb;
     h.o_hbt = ohbt;
     h.o_ghb = oghb;
+    h.o_lin = olin;
     ost += align256((size_t)3 * h.K * h.E * b->rsz);
     orec += align256((size_t)3 * h.NREC * h.E * b->rsz);
     ohb += align256((size_t)h.K * h.E * b->rsz);
     ohbt += align256((size_t)3 * h.P1 * h.E * b->rsz);
     oghb += align256((size_t)2 * h.K1 * h.E * b->rsz);
+    if (b->arith == ARITH_FP64) olin += align256((size_t)2 * h.K * h.K * h.E * b->rsz);
     b->dofs += 3LL * h.K * h.E;
     b->inst.push_back(h);
   }
@@ -287,6 +290,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   alloc(&b->hb, ohb);
   alloc(&b->hbt, ohbt);
   alloc(&b->ghb, oghb);
+  if (olin) alloc(&b->lin, olin);
   alloc((void**)&b->lam, sizeof(double) * 2 * n);
   alloc((void**)&b->t, sizeof(double) * n);
   alloc((void**)&b->err, sizeof(unsigned));
@@ -310,13 +314,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     BatchInst& d = desc[i];
     std::memset(&d, 0, sizeof d);
     const double hx = h.cfg.Lx / h.cfg.nx, hy = h.cfg.Ly / h.cfg.ny;
-    d.m.nx = h.cfg.nx;
-    d.m.ny = h.cfg.ny;
-    d.m.E = h.E;
-    d.m.hx = hx;
-    d.m.hy = hy;
-    d.m.diag = std::hypot(hx, hy);
-    d.m.periodic = h.cfg.bc == DG_BC_PERIODIC;
+    d.m = make_mesh(h.cfg.nx, h.cfg.ny, h.cfg.x0, h.cfg.y0, h.cfg.Lx, h.cfg.Ly, h.cfg.bc == DG_BC_PERIODIC);
     d.g = h.cfg.g;
     d.inv_det = 1.0 / (hx * hy);
     d.det = hx * hy;
@@ -333,6 +331,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     d.hb = (char*)b->hb + h.o_hb;
     d.hbt = (char*)b->hbt + h.o_hbt;
     d.ghb = (char*)b->ghb + h.o_ghb;
+    d.lin = b->lin ? (char*)b->lin + h.o_lin : nullptr;
     d.lam = b->lam + i;
     d.t = b->t + i;
     d.p = h.p;
@@ -341,11 +340,12 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     if ((st = store_real(b, (const double*)d_xi[i], w0, KE, s)) != DG_OK) break;
     if ((st = store_real(b, (const double*)d_qx[i], w0 + KE * b->rsz, KE, s)) != DG_OK) break;
     if ((st = store_real(b, (const double*)d_qy[i], w0 + 2 * KE * b->rsz, KE, s)) != DG_OK) break;
-    void *ph = (void*)d.hb, *pt = (void*)d.hbt, *pg = (void*)d.ghb;
+    void *ph = (void*)d.hb, *pt = (void*)d.hbt, *pg = (void*)d.ghb, *pl = (void*)d.lin;
+    const double* hbi = (const double*)d_hb[i];
     switch (b->arith) {
-      case ARITH_FP64: e = static_fp64(h.p, d.m, (const double*)d_hb[i], ph, pt, pg, s); break;
-      case ARITH_FP32_P64: e = static_fp32p64(h.p, d.m, (const double*)d_hb[i], ph, pt, pg, s); break;
-      default: e = static_fp32p32(h.p, d.m, (const double*)d_hb[i], ph, pt, pg, s); break;
+      case ARITH_FP64: e = static_fp64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, pl, s); break;
+      case ARITH_FP32_P64: e = static_fp32p64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
+      default: e = static_fp32p32(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
     }
   }
   if (e == cudaSuccess && st == DG_OK)

@@ -53,10 +53,20 @@ enum : unsigned { ERRF_DRY = 1u, ERRF_NONFINITE = 2u };
 struct Mesh {
   int nx, ny;
   long long E;
+  double x0, y0;   // domain origin
   double hx, hy;   // quad sizes
   double diag;     // sqrt(hx^2 + hy^2)
-  int periodic;    // 1 periodic, 0 reflective walls
+  double ndx, ndy; // hy / diag, hx / diag: unit normal of the lower diagonal
+  int periodic;    // 1 periodic, 0 walls
+  // per-element geometry of a general (e.g. randomly perturbed) quad-split
+  // mesh, [NGEO][E] FP64; null for the uniform mesh (computed from e)
+  const double* geo;
 };
+
+// per-element geometry record (general meshes): adj(B)^T = G, |det B|,
+// 1/|det B|, (n_x, n_y, |E|) of the three local edges, vertex a1
+enum { GEO_G11 = 0, GEO_G12, GEO_G21, GEO_G22, GEO_DET, GEO_IDET, GEO_EDGE, GEO_A1X = GEO_EDGE + 9, GEO_A1Y,
+       NGEO };
 
 // neighbour across local edge n (same local index on the other side); -1 = wall
 __device__ __forceinline__ long long neighbour(const Mesh& m, long long e, int n) {
@@ -78,12 +88,18 @@ __device__ __forceinline__ long long neighbour(const Mesh& m, long long e, int n
 // Outward unit normal and length of local edge n.  Lower triangle: edge 0 is
 // the diagonal (normal (hy, hx)/diag), edge 1 the left side (-1, 0), edge 2
 // the bottom (0, -1); the upper triangle has the opposite normals.
-template <class Real>
-__device__ __forceinline__ void edge_geom(const Mesh& m, int t, int n, Real& nx, Real& ny, Real& len) {
+template <int FEAT, class Real>
+__device__ __forceinline__ void edge_geom(const Mesh& m, long long e, int t, int n, Real& nx, Real& ny, Real& len) {
+  if (FEAT && m.geo) {
+    nx = Real(m.geo[(GEO_EDGE + 3 * n) * m.E + e]);
+    ny = Real(m.geo[(GEO_EDGE + 3 * n + 1) * m.E + e]);
+    len = Real(m.geo[(GEO_EDGE + 3 * n + 2) * m.E + e]);
+    return;
+  }
   const Real s = t ? Real(-1) : Real(1);
   if (n == 0) {
-    nx = s * Real(m.hy / m.diag);
-    ny = s * Real(m.hx / m.diag);
+    nx = s * Real(m.ndx);
+    ny = s * Real(m.ndy);
     len = Real(m.diag);
   } else if (n == 1) {
     nx = -s;
@@ -94,6 +110,90 @@ __device__ __forceinline__ void edge_geom(const Mesh& m, int t, int n, Real& nx,
     ny = -s;
     len = Real(m.hx);
   }
+}
+
+// adj(B)^T of element e: diagonal (hy, hx) for the lower, -(hy, hx) for the
+// upper triangle of the uniform mesh; read from the geometry record otherwise
+template <int FEAT, class Real>
+__device__ __forceinline__ void elem_G(const Mesh& m, long long e, int t, Real& G11, Real& G12, Real& G21,
+                                       Real& G22) {
+  if (FEAT && m.geo) {
+    G11 = Real(m.geo[GEO_G11 * m.E + e]);
+    G12 = Real(m.geo[GEO_G12 * m.E + e]);
+    G21 = Real(m.geo[GEO_G21 * m.E + e]);
+    G22 = Real(m.geo[GEO_G22 * m.E + e]);
+    return;
+  }
+  const Real sgn = t ? Real(-1) : Real(1);
+  G11 = sgn * Real(m.hy);
+  G22 = sgn * Real(m.hx);
+  G12 = Real(0);
+  G21 = Real(0);
+}
+
+template <int FEAT>
+__device__ __forceinline__ double elem_inv_det(const Mesh& m, long long e, double uniform) {
+  return (FEAT && m.geo) ? m.geo[GEO_IDET * m.E + e] : uniform;
+}
+
+// affine map x = a1 + B x^ of element e (FP64)
+__device__ __forceinline__ void elem_map(const Mesh& m, long long e, double& ax, double& ay, double& B11,
+                                         double& B12, double& B21, double& B22) {
+  if (m.geo) {
+    ax = m.geo[GEO_A1X * m.E + e];
+    ay = m.geo[GEO_A1Y * m.E + e];
+    // G = adj(B)^T = [[B22, -B21], [-B12, B11]]
+    B11 = m.geo[GEO_G22 * m.E + e];
+    B22 = m.geo[GEO_G11 * m.E + e];
+    B21 = -m.geo[GEO_G12 * m.E + e];
+    B12 = -m.geo[GEO_G21 * m.E + e];
+    return;
+  }
+  const int t = (int)(e & 1);
+  const long long q = e >> 1;
+  const int i = (int)(q % m.nx), j = (int)(q / m.nx);
+  B12 = 0.0;
+  B21 = 0.0;
+  if (t == 0) {
+    ax = m.x0 + i * m.hx;
+    ay = m.y0 + j * m.hy;
+    B11 = m.hx;
+    B22 = m.hy;
+  } else {
+    ax = m.x0 + (i + 1) * m.hx;
+    ay = m.y0 + (j + 1) * m.hy;
+    B11 = -m.hx;
+    B22 = -m.hy;
+  }
+}
+
+// §3.1 analytic solution (C_a = C_t = 0.2, y_a = 0.3) and the body force F
+// that makes it satisfy Eq. (2) with tau_bf = f_c = 0 on the bathymetry
+// h_b = 1 + x/1000 + 2 y/1000.
+__device__ __forceinline__ void ms_state(double x, double y, double t, double& xi, double& U, double& V) {
+  const double S = sin(3.141592653589793 * (x + y + 0.2 * t) / 600.0);
+  xi = 2.3 - 0.4 * S;
+  U = 0.6 + 0.04 * S;
+  V = 0.3 + 0.04 * S;
+}
+
+__device__ __forceinline__ void ms_force(double x, double y, double t, double g, double& Fx, double& Fy) {
+  const double k = 3.141592653589793 / 600.0;
+  const double th = k * (x + y + 0.2 * t);
+  double S, C;
+  sincos(th, &S, &C);
+  const double xi = 2.3 - 0.4 * S, U = 0.6 + 0.04 * S, V = 0.3 + 0.04 * S;
+  const double H = xi + 1.0 + x / 1000.0 + 2.0 * y / 1000.0;
+  const double xix = -0.4 * k * C;                  // = d xi / dy
+  const double qx = 0.04 * k * C, qt = 0.04 * 0.2 * k * C;   // dU/dx = dU/dy = dV/dx = dV/dy; dU/dt = dV/dt
+  const double Hx = xix + 1.0e-3, Hy = xix + 2.0e-3;
+  // F = d_t q + div(q q^T / H) + g H grad xi
+  const double dUU_dx = 2.0 * U * qx / H - U * U * Hx / (H * H);
+  const double dUV_dy = (qx * V + U * qx) / H - U * V * Hy / (H * H);
+  const double dUV_dx = (qx * V + U * qx) / H - U * V * Hx / (H * H);
+  const double dVV_dy = 2.0 * V * qx / H - V * V * Hy / (H * H);
+  Fx = qt + dUU_dx + dUV_dy + g * H * xix;
+  Fy = qt + dUV_dx + dVV_dy + g * H * xix;
 }
 
 // ---------------------------------------------------------------------------
@@ -156,6 +256,58 @@ __device__ __forceinline__ void momentum_products(const R* U, const R* V, const 
     Puv[CV(n)] = auv;
     Pvu[CV(n)] = avu;
     Pvv[CV(n)] = avv;
+  });
+}
+
+// out[n] = sum_{i,m} T[n][i][m] a_i a_m for n < NOUT, using the symmetry of
+// T in (i, m): sum_i a_i (T[n][i][i] a_i + 2 sum_{m>i} T[n][i][m] a_m)
+template <int P, int NOUT, class R>
+__device__ __forceinline__ void tprod_sym(const R* a, R* out) {
+  using Tb = RefTables<P>;
+  constexpr int K = Tb::K;
+  sfor<0, NOUT>([&](auto n) {
+    R acc = R(0);
+    sfor<0, K>([&](auto i) {
+      R inner = R(0);
+      bool any = false;
+      sfor<CV(i), K>([&](auto m) {
+        constexpr double t = Tb::T[CV(n)][CV(i)][CV(m)] * (CV(m) == CV(i) ? 1.0 : 2.0);
+        if constexpr (t != 0.0) {
+          inner = fma(R(t), a[CV(m)], inner);
+          any = true;
+        }
+      });
+      if (any) acc = fma(a[CV(i)], inner, acc);
+    });
+    out[CV(n)] = acc;
+  });
+}
+
+// the two edge momentum products Pi(x u_n), Pi(y u_n) sharing the inner sums
+// sum_b Lam[j][a][b] u_n,b
+template <int P, class R>
+__device__ __forceinline__ void lprod2(const R* x, const R* y, const R* un, R* ox, R* oy) {
+  using Tb = RefTables<P>;
+  constexpr int P1 = Tb::P1;
+  sfor<0, P1>([&](auto j) {
+    R ax = R(0), ay = R(0);
+    sfor<0, P1>([&](auto a) {
+      R inner = R(0);
+      bool any = false;
+      sfor<0, P1>([&](auto b) {
+        constexpr double c = Tb::Lam[CV(j)][CV(a)][CV(b)];
+        if constexpr (c != 0.0) {
+          inner = fma(R(c), un[CV(b)], inner);
+          any = true;
+        }
+      });
+      if (any) {
+        ax = fma(x[CV(a)], inner, ax);
+        ay = fma(y[CV(a)], inner, ay);
+      }
+    });
+    ox[CV(j)] = ax;
+    oy[CV(j)] = ay;
   });
 }
 
@@ -296,6 +448,42 @@ __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R
   return ok;
 }
 
+// phi^_i(x^, y^), i < K, from the exact monomial tables
+template <int K>
+__device__ __forceinline__ void basis_at(double xr, double yr, double* phi) {
+  double xp[5], yp[5];
+  xp[0] = yp[0] = 1.0;
+  for (int k = 1; k < 5; ++k) {
+    xp[k] = xp[k - 1] * xr;
+    yp[k] = yp[k - 1] * yr;
+  }
+  sfor<0, K>([&](auto i) {
+    double v = 0.0;
+    sfor<0, 5>([&](auto a) {
+      sfor<0, 5 - CV(a)>([&](auto b) {
+        constexpr double c = BasisMonomials::c[CV(i)][CV(a)][CV(b)];
+        if constexpr (c != 0.0) v = fma(c, xp[CV(a)] * yp[CV(b)], v);
+      });
+    });
+    phi[CV(i)] = v;
+  });
+}
+
+// reference point of local edge NN at s in [0, 1] (counter-clockwise)
+template <int NN>
+__device__ __forceinline__ void edge_ref(double s, double& xr, double& yr) {
+  if constexpr (NN == 0) {
+    xr = 1.0 - s;
+    yr = s;
+  } else if constexpr (NN == 1) {
+    xr = 0.0;
+    yr = 1.0 - s;
+  } else {
+    xr = s;
+    yr = 0.0;
+  }
+}
+
 // ---------------------------------------------------------------------------
 template <class Real>
 struct StageParams {
@@ -316,16 +504,27 @@ struct StageParams {
   const Real* hb;     // [K][E]
   const Real* hbt;    // [3][P1][E] bathymetry traces
   const Real* ghb;    // [2][K1][E] det-scaled bathymetry gradient coefficients
+  const Real* lin;    // FP64 only: [2][K][K][E] matrices of the terms linear in xi
+                      // (g xi grad h_b source + g Pi(xi h_b) pressure part)
   // time step
   double dt_fixed;    // > 0: fixed step
   double cfl_num;     // cfl * d_min / (2p + 1)
   const double* lam;  // max wave speed of this step's initial state
   double* lam_next;   // accumulator of the evaluated state's wave speed (or null)
   double* lam_clear;  // slot zeroed by thread 0 (or null)
-  double* t;          // time, advanced by dt by thread 0 (or null)
   double inv_det;     // 1 / |det B| (uniform mesh)
   double det;         // |det B|
   double tau_bf, f_c; // bottom friction and Coriolis (Eq. (2)); both 0 = off
+  // §3.1 manufactured solution: body force in the volume, exact Dirichlet
+  // data as the ghost state of boundary edges (evaluated at the stage time)
+  int forcing;
+  int dirichlet;
+  const double* t_now; // time at the start of the step (device scalar)
+  double c_eval;       // time of the evaluated state: t_now + c_eval * dt
+  const double* vq;    // volume rule [3][nqv]: x^, y^, weight
+  int nqv;
+  const double* eq;    // edge rule [nqe][7]: s, weight, L_0(s) .. L_4(s)
+  int nqe;
   unsigned* err;      // error word (ERRF_* bits)
   Real* rhs_out;      // mode MODE_RHS output [3][K][E]
 };
@@ -337,6 +536,82 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long*>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
+// Boundary edge with exact Dirichlet data (§3.1 solution at the stage time):
+// the ghost state is the exact (xi, U, V) with h_b+ = h_b- and u+ = q+/H+,
+// so the flux is not polynomial; it is integrated with the Gauss rule sp.eq
+// (the same number of points as the reference scheme) and stored as
+// |E| * its Legendre coefficients in the flux slots of the side record.
+template <int NN, int P, class Real>
+__device__ __forceinline__ void dirichlet_flux(const StageParams<Real>& sp, long long e, Real nx, Real ny, Real len,
+                                               const Real* tx, const Real* tU, const Real* tV, const Real* tu,
+                                               const Real* tv, const Real* th, const Real* un, const Real* Hs,
+                                               Real* rb, double t_eval, unsigned& err) {
+  constexpr int P1 = P + 1;
+  const long long E = sp.m.E;
+  const double g = double(sp.g), nxd = double(nx), nyd = double(ny);
+  double ax, ay, B11, B12, B21, B22;
+  elem_map(sp.m, e, ax, ay, B11, B12, B21, B22);
+  auto point = [&](double s, double& x, double& y) {
+    double xr, yr;
+    edge_ref<NN>(s, xr, yr);
+    x = ax + B11 * xr + B12 * yr;
+    y = ay + B21 * xr + B22 * yr;
+  };
+  auto evalL = [&](const Real* tau, const double* L) {
+    double v = 0.0;
+    for (int j = 0; j < P1; ++j) v = fma(double(tau[j]), L[j], v);
+    return v;
+  };
+  // wave speed: both sides at s = 0, 1/2, 1
+  double lam = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double s = 0.5 * k;
+    double L[P1], pp = 1.0, pc = 2.0 * s - 1.0;   // orthonormal shifted Legendre at s
+    L[0] = 1.0;
+    if (P1 > 1) L[1] = sqrt(3.0) * pc;
+    for (int j = 1; j + 1 < P1; ++j) {
+      const double pn = ((2 * j + 1) * (2.0 * s - 1.0) * pc - j * pp) / (j + 1);
+      pp = pc;
+      pc = pn;
+      L[j + 1] = sqrt(2.0 * (j + 1) + 1.0) * pn;
+    }
+    const double Hin = evalL(Hs, L), unin = evalL(un, L), hbin = evalL(th, L);
+    double x, y, xg, Ug, Vg;
+    point(s, x, y);
+    ms_state(x, y, t_eval, xg, Ug, Vg);
+    const double Hg = xg + hbin;
+    if (!(Hin > 0.0) || !(Hg > 0.0)) err |= ERRF_DRY;
+    lam = fmax(lam, fabs(unin) + sqrt(g * Hin));
+    lam = fmax(lam, fabs((Ug * nxd + Vg * nyd) / Hg) + sqrt(g * Hg));
+  }
+  double acc[3][P1];
+  for (int f = 0; f < 3; ++f)
+    for (int j = 0; j < P1; ++j) acc[f][j] = 0.0;
+  for (int q = 0; q < sp.nqe; ++q) {
+    const double* row = sp.eq + 7 * q;
+    const double s = row[0], w = row[1];
+    const double* L = row + 2;
+    const double xi_m = evalL(tx, L), U_m = evalL(tU, L), V_m = evalL(tV, L);
+    const double u_m = evalL(tu, L), v_m = evalL(tv, L), hb = evalL(th, L);
+    double x, y, xi_p, U_p, V_p;
+    point(s, x, y);
+    ms_state(x, y, t_eval, xi_p, U_p, V_p);
+    const double Hp = xi_p + hb, u_p = U_p / Hp, v_p = V_p / Hp;
+    // A~(c).n of Eq. (8) on both sides
+    const double un_m = u_m * nxd + v_m * nyd, un_p = u_p * nxd + v_p * nyd;
+    const double pr_m = 0.5 * g * xi_m * (xi_m + 2.0 * hb), pr_p = 0.5 * g * xi_p * (xi_p + 2.0 * hb);
+    const double fm[3] = {U_m * nxd + V_m * nyd, U_m * un_m + pr_m * nxd, V_m * un_m + pr_m * nyd};
+    const double fp[3] = {U_p * nxd + V_p * nyd, U_p * un_p + pr_p * nxd, V_p * un_p + pr_p * nyd};
+    const double cm[3] = {xi_m, U_m, V_m}, cp[3] = {xi_p, U_p, V_p};
+    for (int f = 0; f < 3; ++f) {
+      const double Fh = 0.5 * (fm[f] + fp[f]) + 0.5 * lam * (cm[f] - cp[f]);
+      for (int j = 0; j < P1; ++j) acc[f][j] = fma(w * Fh, L[j], acc[f][j]);
+    }
+  }
+  for (int f = 0; f < 3; ++f)
+    for (int j = 0; j < P1; ++j) rb[(f * P1 + j) * E] = Real(double(len) * acc[f][j]);
+}
+
 // Side record of local edge NN of element e for the state (xi, U, V, u, v):
 //   [0..P1)      (|E|/2) q.n                       (flux of xi, Eq. (8))
 //   [P1..2P1)    (|E|/2) (Pi(U u_n) + g/2 n_x Pi(xi (xi + 2 h_b)))
@@ -345,15 +620,15 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 //   [6P1]        max over s = 0, 1/2, 1 of |u.n| + sqrt(g H)
 // all edge polynomials in the orthonormal Legendre basis of the edge in the
 // element's own (counter-clockwise) direction.
-template <int NN, int P, class Real>
+template <int NN, int P, int FEAT, class Real>
 __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long long e, int t, const Real* xi,
                                             const Real* U, const Real* V, const Real* u, const Real* v,
-                                            unsigned& err) {
+                                            unsigned& err, double t_eval) {
   using D = Dims<P>;
   constexpr int P1 = D::P1, NREC = D::NREC;
   const long long E = sp.m.E;
   Real nx, ny, len;
-  edge_geom(sp.m, t, NN, nx, ny, len);
+  edge_geom<FEAT>(sp.m, e, t, NN, nx, ny, len);
   const Real hl = Real(0.5) * len;
   const Real hg = Real(0.5) * sp.g;
   Real tx[P1], tU[P1], tV[P1], th[P1], xe[P1], Hs[P1];
@@ -369,8 +644,9 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
   Real Pp[P1], PU[P1], PV[P1], un[P1];
   lprod<P>(tx, xe, Pp);
   Real* rb = sp.rec_out + (long long)NN * NREC * E + e;
-  if constexpr (NN == 0) {
-    // diagonal: n = s (hy, hx) / diag
+  const bool dir_edge = FEAT && sp.dirichlet && NN != 0 && neighbour(sp.m, e, NN) < 0;
+  if (NN == 0 || (FEAT && (sp.m.geo || dir_edge))) {
+    // general edge (the diagonal, any edge of a general mesh, a Dirichlet edge)
     Real tu[P1], tv[P1], qn[P1];
     trace<NN, P>(u, tu);
     trace<NN, P>(v, tv);
@@ -379,21 +655,24 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
       un[jj] = fma(nx, tu[jj], ny * tv[jj]);
       qn[jj] = fma(nx, tU[jj], ny * tV[jj]);
     });
-    lprod<P>(tU, un, PU);
-    lprod<P>(tV, un, PV);
-    sfor<0, P1>([&](auto j) {
-      constexpr int jj = CV(j);
-      rb[(0 * P1 + jj) * E] = hl * qn[jj];
-      rb[(1 * P1 + jj) * E] = hl * fma(hg * nx, Pp[jj], PU[jj]);
-      rb[(2 * P1 + jj) * E] = hl * fma(hg * ny, Pp[jj], PV[jj]);
-    });
-  } else {
+    if constexpr (FEAT) {
+      if (dir_edge) dirichlet_flux<NN, P>(sp, e, nx, ny, len, tx, tU, tV, tu, tv, th, un, Hs, rb, t_eval, err);
+    }
+    if (!dir_edge) {
+      lprod2<P>(tU, tV, un, PU, PV);
+      sfor<0, P1>([&](auto j) {
+        constexpr int jj = CV(j);
+        rb[(0 * P1 + jj) * E] = hl * qn[jj];
+        rb[(1 * P1 + jj) * E] = hl * fma(hg * nx, Pp[jj], PU[jj]);
+        rb[(2 * P1 + jj) * E] = hl * fma(hg * ny, Pp[jj], PV[jj]);
+      });
+    }
+  } else if constexpr (NN != 0) {
     // axis-aligned: n = -s e_x (edge 1) or -s e_y (edge 2), s = +1 lower,
     // -1 upper; u.n = -s u_1 (or -s v), and the sign folds into the scale
     const Real sh = (t ? Real(1) : Real(-1)) * hl;   // -s |E|/2
     trace<NN, P>(NN == 1 ? u : v, un);               // u.n up to the sign -s
-    lprod<P>(tU, un, PU);
-    lprod<P>(tV, un, PV);
+    lprod2<P>(tU, tV, un, PU, PV);
     sfor<0, P1>([&](auto j) {
       constexpr int jj = CV(j);
       if constexpr (NN == 1) {
@@ -426,9 +705,9 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
 // Evaluation of one element's state: velocity projection, volume + source
 // integrals -> vs_out, side records -> rec_out; returns the element wave
 // speed |q_bar/H_bar| + sqrt(g H_bar) from the means (mean = sqrt(2) c_1).
-template <int P, class Real, class PR>
+template <int P, class Real, class PR, int FEAT>
 __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long long e, int t, const Real* xi,
-                                           const Real* U, const Real* V, unsigned& err) {
+                                           const Real* U, const Real* V, unsigned& err, double t_eval) {
   using D = Dims<P>;
   constexpr int K = D::K, K1 = D::K1;
   const long long E = sp.m.E;
@@ -441,40 +720,86 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
 
   // volume integrals (A~, grad phi_a) (Eqs. (15)-(16)): grad phi_a lies in
   // P^{p-1}, so only the first K1 coefficients of each projected product count
-  Real xe[K];
-  sfor<0, K>([&](auto i) { xe[CV(i)] = fma(Real(2), hb[CV(i)], xi[CV(i)]); });
+  constexpr bool kLin = std::is_same<Real, double>::value;
   Real Puu[K1], Puv[K1], Pvu[K1], Pvv[K1], Pxx[K1];
   momentum_products<P>(U, V, u, v, Puu, Puv, Pvu, Pvv);
-  tprod<P, K1, K>(xi, xe, Pxx);
+  // pressure 1/2 g xi (xi + 2 h_b): in FP64 the part g xi h_b, linear in xi,
+  // and the source g xi grad h_b of Eq. (5) come from the static matrices
+  // sp.lin (fewer FP64 operations), leaving the symmetric Pi(xi xi)
+  Real Sx[K], Sy[K];
+  if constexpr (kLin) {
+    tprod_sym<P, K1>(xi, Pxx);
+  } else {
+    Real xe[K];
+    sfor<0, K>([&](auto i) { xe[CV(i)] = fma(Real(2), hb[CV(i)], xi[CV(i)]); });
+    tprod<P, K1, K>(xi, xe, Pxx);
+    // g sum_{i,m} T[a][i][m] xi_i ghb_m, ghb = det B * coefficients of grad h_b
+    Real gx[K1], gy[K1];
+    sfor<0, K1>([&](auto m) {
+      gx[CV(m)] = sp.ghb[CV(m) * E + e];
+      gy[CV(m)] = sp.ghb[(K1 + CV(m)) * E + e];
+    });
+    tprod<P, K, K1>(xi, gx, Sx);
+    tprod<P, K, K1>(xi, gy, Sy);
+  }
   const Real hg = Real(0.5) * sp.g;
   Real FxU[K1], FyV[K1];
   sfor<0, K1>([&](auto i) {
     FxU[CV(i)] = fma(hg, Pxx[CV(i)], Puu[CV(i)]);
     FyV[CV(i)] = fma(hg, Pxx[CV(i)], Pvv[CV(i)]);
   });
-  // source g xi grad h_b of Eq. (5): g sum_{i,m} T[a][i][m] xi_i ghb_m, with
-  // ghb = det B * (coefficients of grad h_b), which live in P^{p-1}
-  Real gx[K1], gy[K1];
-  sfor<0, K1>([&](auto m) {
-    gx[CV(m)] = sp.ghb[CV(m) * E + e];
-    gy[CV(m)] = sp.ghb[(K1 + CV(m)) * E + e];
-  });
-  Real Sx[K], Sy[K];
-  tprod<P, K, K1>(xi, gx, Sx);
-  tprod<P, K, K1>(xi, gy, Sy);
-  // adj(B)^T of the uniform mesh is diagonal: (hy, hx) lower, -(hy, hx) upper
-  const Real sgn = t ? Real(-1) : Real(1);
-  const Real G11 = sgn * Real(sp.m.hy), G22 = sgn * Real(sp.m.hx);
+  // body force of the §3.1 solution: (F, phi_a) = |det B| sum_q w_q F(x_q) phi^_a(x^_q)
+  double fU[K], fV[K];
+  if (FEAT && sp.forcing) {
+    sfor<0, K>([&](auto a) {
+      fU[CV(a)] = 0.0;
+      fV[CV(a)] = 0.0;
+    });
+    double ax, ay, B11, B12, B21, B22;
+    elem_map(sp.m, e, ax, ay, B11, B12, B21, B22);
+    const double det = B11 * B22 - B12 * B21;
+    for (int q = 0; q < sp.nqv; ++q) {
+      const double xr = sp.vq[q], yr = sp.vq[sp.nqv + q], w = sp.vq[2 * sp.nqv + q] * det;
+      double phi[K], Fx, Fy;
+      basis_at<K>(xr, yr, phi);
+      ms_force(ax + B11 * xr + B12 * yr, ay + B21 * xr + B22 * yr, t_eval, double(sp.g), Fx, Fy);
+      sfor<0, K>([&](auto a) {
+        fU[CV(a)] = fma(w * Fx, phi[CV(a)], fU[CV(a)]);
+        fV[CV(a)] = fma(w * Fy, phi[CV(a)], fV[CV(a)]);
+      });
+    }
+  }
+  // (F, grad phi_a) = sum_r sum_i S[r][a][i] (G_1r F^x_i + G_2r F^y_i)
+  Real G11, G12, G21, G22;
+  elem_G<FEAT>(sp.m, e, t, G11, G12, G21, G22);
+  const bool full_G = FEAT && sp.m.geo != nullptr;   // off-diagonal terms vanish on the uniform mesh
   sfor<0, K>([&](auto a) {
     constexpr int aa = CV(a);
     Real v0 = G11 * sdot_row<P, 0, aa>(U) + G22 * sdot_row<P, 1, aa>(V);
     Real v1 = G11 * sdot_row<P, 0, aa>(FxU) + G22 * sdot_row<P, 1, aa>(Puv);
     Real v2 = G11 * sdot_row<P, 0, aa>(Pvu) + G22 * sdot_row<P, 1, aa>(FyV);
-    v1 = fma(sp.g, Sx[aa], v1);
-    v2 = fma(sp.g, Sy[aa], v2);
+    if (full_G) {
+      v0 += G12 * sdot_row<P, 1, aa>(U) + G21 * sdot_row<P, 0, aa>(V);
+      v1 += G12 * sdot_row<P, 1, aa>(FxU) + G21 * sdot_row<P, 0, aa>(Puv);
+      v2 += G12 * sdot_row<P, 1, aa>(Pvu) + G21 * sdot_row<P, 0, aa>(FyV);
+    }
+    if constexpr (kLin) {
+      sfor<0, K>([&](auto k) {
+        v1 = fma(sp.lin[((0 * K + aa) * K + CV(k)) * E + e], xi[CV(k)], v1);
+        v2 = fma(sp.lin[((1 * K + aa) * K + CV(k)) * E + e], xi[CV(k)], v2);
+      });
+    } else {
+      v1 = fma(sp.g, Sx[aa], v1);
+      v2 = fma(sp.g, Sy[aa], v2);
+    }
+    if (FEAT && sp.forcing) {
+      v1 += Real(fU[aa]);
+      v2 += Real(fV[aa]);
+    }
     if (sp.tau_bf != 0.0 || sp.f_c != 0.0) {
       // (-tau_bf q + f_c (V, -U), phi_a) = |det B| (-tau_bf U_a + f_c V_a, ...)
-      const Real tq = Real(-sp.tau_bf * sp.det), fq = Real(sp.f_c * sp.det);
+      const double det = (FEAT && sp.m.geo) ? sp.m.geo[GEO_DET * sp.m.E + e] : sp.det;
+      const Real tq = Real(-sp.tau_bf * det), fq = Real(sp.f_c * det);
       v1 = fma(tq, U[aa], fma(fq, V[aa], v1));
       v2 = fma(tq, V[aa], fma(-fq, U[aa], v2));
     }
@@ -482,9 +807,9 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
     sp.vs_out[(1 * K + aa) * E + e] = v1;
     sp.vs_out[(2 * K + aa) * E + e] = v2;
   });
-  side_record<0, P>(sp, e, t, xi, U, V, u, v, err);
-  side_record<1, P>(sp, e, t, xi, U, V, u, v, err);
-  side_record<2, P>(sp, e, t, xi, U, V, u, v, err);
+  side_record<0, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval);
+  side_record<1, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval);
+  side_record<2, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval);
   double lam_e = 0.0;
   if (sp.lam_next) {
     const double Hm = double(H[0]);
@@ -496,7 +821,7 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
 
 // Numerical flux on local edge NN and its lift: res[f][a] -= sum_j R[NN][j][a] F^_f,j
 // with F^ = |E| (1/2 (A~(c-) + A~(c+)).n + 1/2 lambda (c- - c+)) (Lax-Friedrichs).
-template <int NN, int P, class Real>
+template <int NN, int P, int FEAT, class Real>
 __device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long long e, int t,
                                                Real (&res)[3][Dims<P>::K]) {
   using D = Dims<P>;
@@ -508,7 +833,7 @@ __device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long
   if (f >= 0) {
     const Real* rn = sp.rec + (long long)NN * NREC * E + f;
     Real nx, ny, len;
-    edge_geom(sp.m, t, NN, nx, ny, len);
+    edge_geom<FEAT>(sp.m, e, t, NN, nx, ny, len);
     const Real lam = fmax(ro[(6 * P1) * E], rn[(6 * P1) * E]);
     const Real hl = Real(0.5) * len * lam;
     // the neighbour's polynomials run the other way (s -> 1 - s flips the sign
@@ -525,11 +850,16 @@ __device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long
         F[fv][jj] = fma(hl, jmp, phi);
       });
     });
+  } else if (FEAT && sp.dirichlet) {
+    // Dirichlet edge: the side record holds the full |E| F^ (see dirichlet_flux)
+    sfor<0, 3>([&](auto ff) {
+      sfor<0, P1>([&](auto j) { F[CV(ff)][CV(j)] = ro[(CV(ff) * P1 + CV(j)) * E]; });
+    });
   } else {
     // reflective wall, mirror ghost: F^(xi) = 0 and
     // F^(q) = |E| n (Pi(q.n u.n) + g/2 Pi(xi (xi + 2 h_b)) + lambda q.n)
     Real nx, ny, len;
-    edge_geom(sp.m, t, NN, nx, ny, len);
+    edge_geom<FEAT>(sp.m, e, t, NN, nx, ny, len);
     const Real lam = ro[(6 * P1) * E];
     sfor<0, P1>([&](auto j) {
       constexpr int jj = CV(j);
@@ -551,7 +881,7 @@ __device__ __forceinline__ bool finite(Real x) { return isfinite(x); }
 // evaluation of the new state; MODE_EVAL = evaluation only; MODE_RHS = flux
 // and lift of an evaluated state, written as d_t c.  Returns the element's
 // wave speed (0 unless sp.lam_next is set) through lam_e.
-template <int P, class Real, class PR, int MODE>
+template <int P, class Real, class PR, int MODE, int FEAT>
 __device__ __forceinline__ void stage_element(const StageParams<Real>& sp, long long e, double dt, double& lam_e,
                                               unsigned& err) {
   using D = Dims<P>;
@@ -562,18 +892,19 @@ __device__ __forceinline__ void stage_element(const StageParams<Real>& sp, long 
   sfor<0, 3>([&](auto f) {
     sfor<0, K>([&](auto i) { w[CV(f)][CV(i)] = sp.w[(CV(f) * K + CV(i)) * E + e]; });
   });
+  const double t_eval = (FEAT && sp.t_now) ? *sp.t_now + sp.c_eval * dt : 0.0;
   if constexpr (MODE == MODE_EVAL) {
-    lam_e = evaluate<P, Real, PR>(sp, e, t, w[0], w[1], w[2], err);
+    lam_e = evaluate<P, Real, PR, FEAT>(sp, e, t, w[0], w[1], w[2], err, t_eval);
   } else {
     Real res[3][K];
     sfor<0, 3>([&](auto f) {
       sfor<0, K>([&](auto i) { res[CV(f)][CV(i)] = sp.vs[(CV(f) * K + CV(i)) * E + e]; });
     });
-    edge_flux_lift<0, P>(sp, e, t, res);
-    edge_flux_lift<1, P>(sp, e, t, res);
-    edge_flux_lift<2, P>(sp, e, t, res);
+    edge_flux_lift<0, P, FEAT>(sp, e, t, res);
+    edge_flux_lift<1, P, FEAT>(sp, e, t, res);
+    edge_flux_lift<2, P, FEAT>(sp, e, t, res);
     if constexpr (MODE == MODE_RHS) {
-      const Real idet = Real(sp.inv_det);
+      const Real idet = Real(elem_inv_det<FEAT>(sp.m, e, sp.inv_det));
       sfor<0, 3>([&](auto f) {
         sfor<0, K>([&](auto i) { sp.rhs_out[(CV(f) * K + CV(i)) * E + e] = res[CV(f)][CV(i)] * idet; });
       });
@@ -582,7 +913,7 @@ __device__ __forceinline__ void stage_element(const StageParams<Real>& sp, long 
       // evaluated as w0 + beta ((w - w0) + dt R): a constant state stays
       // exactly constant and the result is rounded once (alpha and beta
       // themselves are never rounded to the working precision)
-      const Real b = Real(sp.beta), c = Real(dt * sp.inv_det);
+      const Real b = Real(sp.beta), c = Real(dt * elem_inv_det<FEAT>(sp.m, e, sp.inv_det));
       bool fin = true;
       sfor<0, 3>([&](auto f) {
         sfor<0, K>([&](auto i) {
@@ -600,7 +931,7 @@ __device__ __forceinline__ void stage_element(const StageParams<Real>& sp, long 
         });
       });
       if (!fin) err |= ERRF_NONFINITE;
-      lam_e = evaluate<P, Real, PR>(sp, e, t, w[0], w[1], w[2], err);
+      lam_e = evaluate<P, Real, PR, FEAT>(sp, e, t, w[0], w[1], w[2], err, t_eval);
     }
   }
 }
@@ -622,8 +953,10 @@ __device__ __forceinline__ double block_max(double v) {
 }
 
 // One launch per RK stage (MODE_STAGE), per initial evaluation (MODE_EVAL) or
-// per right-hand side (MODE_RHS).  One thread per element.
-template <int P, class Real, class PR, int MODE>
+// per right-hand side (MODE_RHS).  One thread per element.  FEAT = 0 is the
+// uniform-mesh path; FEAT = 1 adds general meshes, the §3.1 body force and
+// Dirichlet edges (kept out of the fast path's registers and code).
+template <int P, class Real, class PR, int MODE, int FEAT>
 __global__ void __launch_bounds__(128) stage_kernel(const StageParams<Real> sp) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double lam_e = 0.0;
@@ -632,22 +965,20 @@ __global__ void __launch_bounds__(128) stage_kernel(const StageParams<Real> sp) 
   if constexpr (MODE == MODE_STAGE) {
     dt = sp.dt_fixed > 0.0 ? sp.dt_fixed : sp.cfl_num / sp.lam[0];
   }
-  if (e < sp.m.E) stage_element<P, Real, PR, MODE>(sp, e, dt, lam_e, err);
+  if (e < sp.m.E) stage_element<P, Real, PR, MODE, FEAT>(sp, e, dt, lam_e, err);
   if (sp.lam_next) {
     const double l = block_max(lam_e);
     if (threadIdx.x == 0) atomic_max_nonneg(sp.lam_next, l);
   }
   if (err) atomicOr(sp.err, err);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (sp.lam_clear) *sp.lam_clear = 0.0;
-    if (sp.t) *sp.t += dt;
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && sp.lam_clear) *sp.lam_clear = 0.0;
 }
 
 // Static per-element fields of the bathymetry: edge traces and the
 // det-scaled gradient coefficients  ghb_r = G_rr * (d^_r h_b) (uniform mesh).
 template <int P, class Real>
-__global__ void static_kernel(Mesh m, const double* __restrict__ hb64, Real* hb, Real* hbt, Real* ghb) {
+__global__ void static_kernel(Mesh m, double g, const double* __restrict__ hb64, Real* hb, Real* hbt, Real* ghb,
+                              Real* lin) {
   using D = Dims<P>;
   using Tb = RefTables<P>;
   constexpr int K = D::K, P1 = D::P1, K1 = D::K1;
@@ -666,16 +997,57 @@ __global__ void static_kernel(Mesh m, const double* __restrict__ hb64, Real* hb,
     sfor<0, P1>([&](auto j) { hbt[(CV(nn) * P1 + CV(j)) * E + e] = Real(tau[CV(j)]); });
   };
   sfor<0, 3>(tr);
-  const double sgn = t ? -1.0 : 1.0;
-  const double G[2] = {sgn * m.hy, sgn * m.hx};
-  sfor<0, 2>([&](auto r) {
+  double G[2][2];
+  elem_G<1>(m, e, t, G[0][0], G[0][1], G[1][0], G[1][1]);
+  // reference derivative coefficients d_c,m = sum_i S[c][i][m] h_i and the
+  // det-scaled physical gradient gh_r = sum_c G_rc d_c
+  double d[2][K1 > 0 ? K1 : 1];
+  sfor<0, 2>([&](auto c) {
     sfor<0, K1>([&](auto mm) {
       double acc = 0.0;
       sfor<0, K>([&](auto i) {
-        constexpr double s = Tb::S[CV(r)][CV(i)][CV(mm)];
+        constexpr double s = Tb::S[CV(c)][CV(i)][CV(mm)];
         if constexpr (s != 0.0) acc = fma(s, h[CV(i)], acc);
       });
-      ghb[(CV(r) * K1 + CV(mm)) * E + e] = Real(G[CV(r)] * acc);
+      d[CV(c)][CV(mm)] = acc;
+    });
+  });
+  double gh[2][K1 > 0 ? K1 : 1];
+  sfor<0, 2>([&](auto r) {
+    sfor<0, K1>([&](auto mm) {
+      gh[CV(r)][CV(mm)] = G[CV(r)][0] * d[0][CV(mm)] + G[CV(r)][1] * d[1][CV(mm)];
+      ghb[(CV(r) * K1 + CV(mm)) * E + e] = Real(gh[CV(r)][CV(mm)]);
+    });
+  });
+  if (!lin) return;
+  // lin[r][a][k]: coefficient of xi_k in the r-momentum volume + source
+  //   g sum_c G_rc sum_{i<K1} S[c][a][i] sum_m T[i][k][m] h_m  (pressure g xi h_b)
+  // + g sum_m T[a][k][m] gh_r,m                              (source g xi d_r h_b)
+  sfor<0, K>([&](auto a) {
+    sfor<0, K>([&](auto k) {
+      double pres[2] = {0.0, 0.0};
+      sfor<0, 2>([&](auto c) {
+        sfor<0, K1>([&](auto i) {
+          constexpr double s = Tb::S[CV(c)][CV(a)][CV(i)];
+          if constexpr (s != 0.0) {
+            double th = 0.0;
+            sfor<0, K>([&](auto mm) {
+              constexpr double tt = Tb::T[CV(i)][CV(k)][CV(mm)];
+              if constexpr (tt != 0.0) th = fma(tt, h[CV(mm)], th);
+            });
+            pres[CV(c)] = fma(s, th, pres[CV(c)]);
+          }
+        });
+      });
+      sfor<0, 2>([&](auto r) {
+        double src = 0.0;
+        sfor<0, K1>([&](auto mm) {
+          constexpr double tt = Tb::T[CV(a)][CV(k)][CV(mm)];
+          if constexpr (tt != 0.0) src = fma(tt, gh[CV(r)][CV(mm)], src);
+        });
+        const double pr = G[CV(r)][0] * pres[0] + G[CV(r)][1] * pres[1];
+        lin[((CV(r) * K + CV(a)) * K + CV(k)) * E + e] = Real(g * (pr + src));
+      });
     });
   });
 }
@@ -699,6 +1071,7 @@ __global__ void __launch_bounds__(128) diag_kernel(Mesh m, const Real* __restric
       H[CV(i)] = xi[CV(i)] + hb[CV(i) * E + e];
     });
     project_velocity<P, PR>(H, U, V, u, v);
+    if (m.geo) det = m.geo[GEO_DET * E + e];
     ms = det * double(xi[0]) * 0.70710678118654752;
     sfor<0, K>([&](auto i) {
       en += g * double(xi[CV(i)]) * double(xi[CV(i)]) + double(U[CV(i)]) * double(u[CV(i)]) +

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "dg_kernels.cuh"
 
 namespace dgswe {
@@ -13,9 +15,6 @@ enum Arith { ARITH_FP64 = 0, ARITH_FP32_P64 = 1, ARITH_FP32_P32 = 2 };
 
 // Launch one stage_kernel.  params points to a StageParams<double> (FP64) or
 // StageParams<float>.  Returns the launch error.
-cudaError_t launch_stage(int arith, int p, int mode, int block, const void* params, cudaStream_t s);
-cudaError_t launch_static(int arith, int p, const Mesh& m, const double* hb64, void* hb, void* hbt, void* ghb,
-                          cudaStream_t s);
 cudaError_t launch_diag(int arith, int p, const Mesh& m, const void* w, const void* hb, double det, double g,
                         double* partial, cudaStream_t s);
 
@@ -24,13 +23,13 @@ inline long long grid_for(long long E, int block) {
   return (E + block - 1) / block;
 }
 
-// body shared by the per-arithmetic translation units
-#define DGSWE_DEFINE_LAUNCHERS(SUFFIX, REAL, PREAL)                                                        \
+// stage launchers of one arithmetic and feature set (one translation unit each)
+#define DGSWE_DEFINE_STAGE(SUFFIX, REAL, PREAL, FEAT)                                                     \
   template <int P, int MODE>                                                                               \
   static cudaError_t stage_##SUFFIX##_pm(int block, const void* params, cudaStream_t s) {                  \
     const StageParams<REAL>& sp = *static_cast<const StageParams<REAL>*>(params);                          \
     const long long g = (sp.m.E + block - 1) / block;                                                      \
-    stage_kernel<P, REAL, PREAL, MODE><<<(unsigned)g, block, 0, s>>>(sp);                                  \
+    stage_kernel<P, REAL, PREAL, MODE, FEAT><<<(unsigned)g, block, 0, s>>>(sp);                            \
     return cudaGetLastError();                                                                             \
   }                                                                                                        \
   template <int P>                                                                                         \
@@ -47,16 +46,19 @@ inline long long grid_for(long long E, int block) {
       case 4: return stage_##SUFFIX##_p<4>(mode, block, params, s);                                        \
     }                                                                                                      \
     return cudaErrorInvalidValue;                                                                          \
-  }                                                                                                        \
-  cudaError_t static_##SUFFIX(int p, const Mesh& m, const double* hb64, void* hb, void* hbt, void* ghb,    \
-                              cudaStream_t s) {                                                            \
+  }
+
+// set-up and diagnostics launchers of one arithmetic
+#define DGSWE_DEFINE_AUX(SUFFIX, REAL, PREAL)                                                              \
+  cudaError_t static_##SUFFIX(int p, const Mesh& m, double gg, const double* hb64, void* hb, void* hbt,    \
+                              void* ghb, void* lin, cudaStream_t s) {                                      \
     const unsigned g = (unsigned)((m.E + 127) / 128);                                                      \
-    REAL *a = (REAL*)hb, *b = (REAL*)hbt, *c = (REAL*)ghb;                                                 \
+    REAL *a = (REAL*)hb, *b = (REAL*)hbt, *c = (REAL*)ghb, *d = (REAL*)lin;                                \
     switch (p) {                                                                                           \
-      case 1: static_kernel<1, REAL><<<g, 128, 0, s>>>(m, hb64, a, b, c); break;                           \
-      case 2: static_kernel<2, REAL><<<g, 128, 0, s>>>(m, hb64, a, b, c); break;                           \
-      case 3: static_kernel<3, REAL><<<g, 128, 0, s>>>(m, hb64, a, b, c); break;                           \
-      case 4: static_kernel<4, REAL><<<g, 128, 0, s>>>(m, hb64, a, b, c); break;                           \
+      case 1: static_kernel<1, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
+      case 2: static_kernel<2, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
+      case 3: static_kernel<3, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
+      case 4: static_kernel<4, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
       default: return cudaErrorInvalidValue;                                                               \
     }                                                                                                      \
     return cudaGetLastError();                                                                             \
@@ -78,11 +80,35 @@ inline long long grid_for(long long E, int block) {
 cudaError_t stage_fp64(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p64(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p32(int p, int mode, int block, const void* params, cudaStream_t s);
-cudaError_t static_fp64(int p, const Mesh& m, const double* hb64, void* hb, void* hbt, void* ghb, cudaStream_t s);
-cudaError_t static_fp32p64(int p, const Mesh& m, const double* hb64, void* hb, void* hbt, void* ghb,
-                           cudaStream_t s);
-cudaError_t static_fp32p32(int p, const Mesh& m, const double* hb64, void* hb, void* hbt, void* ghb,
-                           cudaStream_t s);
+cudaError_t stage_fp64_gen(int p, int mode, int block, const void* params, cudaStream_t s);
+cudaError_t stage_fp32p64_gen(int p, int mode, int block, const void* params, cudaStream_t s);
+cudaError_t stage_fp32p32_gen(int p, int mode, int block, const void* params, cudaStream_t s);
+// static fields of the bathymetry; lin (FP64 contexts only, else null):
+// [2][K][K][E] matrices of the terms linear in xi
+cudaError_t static_fp64(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb, void* lin,
+                        cudaStream_t s);
+cudaError_t static_fp32p64(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
+                           void* lin, cudaStream_t s);
+cudaError_t static_fp32p32(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
+                           void* lin, cudaStream_t s);
+
+// fill the derived geometry of a uniform mesh
+inline Mesh make_mesh(int nx, int ny, double x0, double y0, double Lx, double Ly, bool periodic) {
+  Mesh m;
+  m.nx = nx;
+  m.ny = ny;
+  m.E = 2LL * nx * ny;
+  m.x0 = x0;
+  m.y0 = y0;
+  m.geo = nullptr;
+  m.hx = Lx / nx;
+  m.hy = Ly / ny;
+  m.diag = std::hypot(m.hx, m.hy);
+  m.ndx = m.hy / m.diag;
+  m.ndy = m.hx / m.diag;
+  m.periodic = periodic ? 1 : 0;
+  return m;
+}
 cudaError_t diag_fp64(int p, const Mesh& m, const void* w, const void* hb, double det, double g, double* partial,
                       cudaStream_t s);
 cudaError_t diag_fp32p64(int p, const Mesh& m, const void* w, const void* hb, double det, double g,

@@ -29,7 +29,7 @@ using namespace dgswe;
 
 namespace {
 
-// 32 MiB: enough for about 43,000 FP64 triangles at p = 2 (768 bytes each).
+// 32 MiB: enough for about 24,000 FP64 triangles at p = 2 (1344 bytes each).
 constexpr size_t kScratchBytes = size_t(32) << 20;
 constexpr size_t kAlign = 256;
 
@@ -68,14 +68,17 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   const int K = (P + 1) * (P + 2) / 2, K1 = P * (P + 1) / 2, P1 = P + 1, NREC = 6 * P1 + 1;
   const long long E = 2LL * cfg->nx * cfg->ny;
   const size_t rs = sizeof(Real);
-  // carve the array: error word, hb, hb traces, hb gradients, vs, records
+  // carve the array: error word, hb, hb traces, hb gradients, vs, records,
+  // and in FP64 the matrices of the terms linear in xi
   const size_t o_err = 0;
   const size_t o_hb = o_err + round_up(sizeof(unsigned));
   const size_t o_hbt = o_hb + round_up((size_t)K * E * rs);
   const size_t o_ghb = o_hbt + round_up((size_t)3 * P1 * E * rs);
   const size_t o_vs = o_ghb + round_up((size_t)2 * K1 * E * rs);
   const size_t o_rec = o_vs + round_up((size_t)3 * K * E * rs);
-  const size_t total = o_rec + round_up((size_t)3 * NREC * E * rs);
+  const size_t o_lin = o_rec + round_up((size_t)3 * NREC * E * rs);
+  const bool fp64 = arith == ARITH_FP64;
+  const size_t total = o_lin + (fp64 ? round_up((size_t)2 * K * K * E * rs) : 0);
   if (total > kScratchBytes) return DG_ERR_ARG;
   void* base = nullptr;
   cudaError_t e = scratch_for_current_device(&base);
@@ -84,19 +87,13 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   unsigned* err = reinterpret_cast<unsigned*>(b + o_err);
   if (cudaMemsetAsync(err, 0, sizeof(unsigned), s) != cudaSuccess) return DG_ERR_CUDA;
 
-  Mesh m;
-  const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
-  m.nx = cfg->nx;
-  m.ny = cfg->ny;
-  m.E = E;
-  m.hx = hx;
-  m.hy = hy;
-  m.diag = std::hypot(hx, hy);
-  m.periodic = cfg->bc == DG_BC_PERIODIC;
+  const Mesh m = make_mesh(cfg->nx, cfg->ny, cfg->x0, cfg->y0, cfg->Lx, cfg->Ly, cfg->bc == DG_BC_PERIODIC);
+  const double hx = m.hx, hy = m.hy;
+  void* lin = fp64 ? (void*)(b + o_lin) : nullptr;
   switch (arith) {
-    case ARITH_FP64: e = static_fp64(P, m, d_hb, b + o_hb, b + o_hbt, b + o_ghb, s); break;
-    case ARITH_FP32_P64: e = static_fp32p64(P, m, d_hb, b + o_hb, b + o_hbt, b + o_ghb, s); break;
-    default: e = static_fp32p32(P, m, d_hb, b + o_hb, b + o_hbt, b + o_ghb, s); break;
+    case ARITH_FP64: e = static_fp64(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, lin, s); break;
+    case ARITH_FP32_P64: e = static_fp32p64(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
+    default: e = static_fp32p32(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
   }
   if (e != cudaSuccess) return DG_ERR_CUDA;
 
@@ -107,6 +104,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   sp.hb = reinterpret_cast<const Real*>(b + o_hb);
   sp.hbt = reinterpret_cast<const Real*>(b + o_hbt);
   sp.ghb = reinterpret_cast<const Real*>(b + o_ghb);
+  sp.lin = static_cast<const Real*>(lin);
   sp.inv_det = 1.0 / (hx * hy);
   sp.det = hx * hy;
   sp.tau_bf = cfg->tau_bf;
@@ -141,6 +139,7 @@ extern "C" dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, cons
       cfg->precision > 1 || cfg->proj_precision < 0 || cfg->proj_precision > 1)
     return DG_ERR_ARG;
   if (cfg->bc == DG_BC_PERIODIC && (cfg->nx < 2 || cfg->ny < 2)) return DG_ERR_ARG;
+  if (cfg->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
   if (cfg->block_size != 0 && (cfg->block_size < 32 || cfg->block_size > 128 || cfg->block_size % 32))
     return DG_ERR_ARG;
   if (2.0 * (double)cfg->nx * (double)cfg->ny > 1.0e8) return DG_ERR_ARG;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <vector>
 
 #include "dg_kernels.cuh"
 #include "dgswe.h"
@@ -105,6 +106,18 @@ __global__ void nodes_kernel(Geo g, Rule r, double* __restrict__ xy) {
   }
 }
 
+// nodes of a general mesh from per-element maps [6][E]: a1x, a1y, B11, B12, B21, B22
+__global__ void nodes_kernel_map(long long E, Rule r, const double* __restrict__ map, double* __restrict__ xy) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  const double ax = map[e], ay = map[E + e], b11 = map[2 * E + e], b12 = map[3 * E + e], b21 = map[4 * E + e],
+               b22 = map[5 * E + e];
+  for (int q = 0; q < r.Q; ++q) {
+    xy[(long long)q * E + e] = ax + b11 * r.xr[q] + b12 * r.yr[q];
+    xy[((long long)r.Q + q) * E + e] = ay + b21 * r.xr[q] + b22 * r.yr[q];
+  }
+}
+
 template <int K>
 __global__ void project_kernel(long long E, Rule r, const double* __restrict__ vals, double* __restrict__ coef) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -134,8 +147,7 @@ __global__ void project_kernel(long long E, Rule r, const double* __restrict__ v
 }
 
 bool geo_of(const dg_config* c, Geo* g) {
-  if (!c || c->nx < 1 || c->ny < 1 || c->p < 0 || c->p > 4 || !(c->Lx > 0) || !(c->Ly > 0) || c->vertex_xy)
-    return false;
+  if (!c || c->nx < 1 || c->ny < 1 || c->p < 0 || c->p > 4 || !(c->Lx > 0) || !(c->Ly > 0)) return false;
   g->nx = c->nx;
   g->E = 2LL * c->nx * c->ny;
   g->x0 = c->x0;
@@ -155,8 +167,42 @@ dg_status dg_proj_nodes(const dg_config* cfg, void* d_xy, void* stream) {
   Geo g;
   if (!geo_of(cfg, &g) || !d_xy) return DG_ERR_ARG;
   const Rule r = make_rule(cfg->p);
-  nodes_kernel<<<(unsigned)((g.E + 127) / 128), 128, 0, (cudaStream_t)stream>>>(g, r, (double*)d_xy);
-  return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+  if (!cfg->vertex_xy) {
+    nodes_kernel<<<(unsigned)((g.E + 127) / 128), 128, 0, (cudaStream_t)stream>>>(g, r, (double*)d_xy);
+    return cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+  }
+  // general mesh: element maps from the vertices (set-up only)
+  const int nx = cfg->nx, ny = cfg->ny;
+  const long long E = g.E;
+  std::vector<double> map((size_t)6 * E);
+  const double* v = cfg->vertex_xy;
+  auto vx = [&](int i, int j) { return v[2 * ((size_t)j * (nx + 1) + i)]; };
+  auto vy = [&](int i, int j) { return v[2 * ((size_t)j * (nx + 1) + i) + 1]; };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int t = 0; t < 2; ++t) {
+        const long long e = 2LL * ((long long)j * nx + i) + t;
+        const int i1 = t ? i + 1 : i, j1 = t ? j + 1 : j;
+        const int i2 = t ? i : i + 1, j2 = t ? j + 1 : j;
+        const int i3 = t ? i + 1 : i, j3 = t ? j : j + 1;
+        map[e] = vx(i1, j1);
+        map[E + e] = vy(i1, j1);
+        map[2 * E + e] = vx(i2, j2) - vx(i1, j1);
+        map[3 * E + e] = vx(i3, j3) - vx(i1, j1);
+        map[4 * E + e] = vy(i2, j2) - vy(i1, j1);
+        map[5 * E + e] = vy(i3, j3) - vy(i1, j1);
+      }
+  double* d = nullptr;
+  if (cudaMalloc(&d, sizeof(double) * map.size()) != cudaSuccess) return DG_ERR_OOM;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(d, map.data(), sizeof(double) * map.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    nodes_kernel_map<<<(unsigned)((E + 127) / 128), 128, 0, s>>>(E, r, d, (double*)d_xy);
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(d);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? DG_OK : DG_ERR_CUDA;
 }
 
 dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, void* stream) {

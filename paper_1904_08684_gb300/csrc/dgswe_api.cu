@@ -2,6 +2,7 @@
 // device buffers, graph-captured time steps, set-up projection, diagnostics.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -38,6 +39,11 @@ struct dg_ctx {
   void* hb;              // [K][E]
   void* hbt;             // [3][P1][E]
   void* ghb;             // [2][K1][E]
+  void* lin;             // FP64 only: [2][K][K][E] terms linear in xi
+  double* geo;           // general meshes: [NGEO][E] per-element geometry
+  double* vq;            // forcing: volume Gauss rule [3][nqv]
+  double* eq;            // forcing: edge Gauss rule [nqe][7]
+  int nqv, nqe;
   double* scal;          // [0],[1]: wave-speed slots, [2]: t, [3]: last dt
   unsigned* err;
   double* partial;       // diagnostics partial sums
@@ -77,17 +83,22 @@ dg_status validate(const dg_config* c) {
   // the stage kernels are compiled for at most 128 threads per block
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 128 || c->block_size % 32)) return DG_ERR_ARG;
   if (c->bc == DG_BC_PERIODIC && (c->nx < 2 || c->ny < 2)) return DG_ERR_ARG;
-  if (c->p == 0 || c->bc == DG_BC_DIRICHLET || c->vertex_xy) return DG_ERR_UNSUPPORTED;
+  if (c->forcing < 0 || c->forcing > 1) return DG_ERR_ARG;
+  if (c->p == 0) return DG_ERR_UNSUPPORTED;
+  if (c->bc == DG_BC_DIRICHLET && c->forcing != DG_FORCING_MANUFACTURED) return DG_ERR_UNSUPPORTED;
+  if (c->vertex_xy && c->bc == DG_BC_PERIODIC) return DG_ERR_UNSUPPORTED;
   if (2.0 * (double)c->nx * (double)c->ny > 4.0e9) return DG_ERR_ARG;
   return DG_OK;
 }
 
 cudaError_t launch_stage_any(const dg_ctx* c, int mode, const void* params, cudaStream_t s) {
   const int block = c->cfg.block_size ? c->cfg.block_size : 128;
+  // general meshes, forcing and Dirichlet edges use the general kernels
+  const bool gen = c->geo || c->cfg.forcing != DG_FORCING_NONE || c->cfg.bc == DG_BC_DIRICHLET;
   switch (c->arith) {
-    case ARITH_FP64: return stage_fp64(c->P, mode, block, params, s);
-    case ARITH_FP32_P64: return stage_fp32p64(c->P, mode, block, params, s);
-    default: return stage_fp32p32(c->P, mode, block, params, s);
+    case ARITH_FP64: return (gen ? stage_fp64_gen : stage_fp64)(c->P, mode, block, params, s);
+    case ARITH_FP32_P64: return (gen ? stage_fp32p64_gen : stage_fp32p64)(c->P, mode, block, params, s);
+    default: return (gen ? stage_fp32p32_gen : stage_fp32p32)(c->P, mode, block, params, s);
   }
 }
 
@@ -100,6 +111,15 @@ StageParams<Real> base_params(const dg_ctx* c) {
   sp.hb = (const Real*)c->hb;
   sp.hbt = (const Real*)c->hbt;
   sp.ghb = (const Real*)c->ghb;
+  sp.lin = (const Real*)c->lin;
+  sp.forcing = c->cfg.forcing == DG_FORCING_MANUFACTURED;
+  sp.dirichlet = c->cfg.bc == DG_BC_DIRICHLET;
+  sp.t_now = c->scal + 2;
+  sp.c_eval = 0.0;
+  sp.vq = c->vq;
+  sp.nqv = c->nqv;
+  sp.eq = c->eq;
+  sp.nqe = c->nqe;
   sp.dt_fixed = c->cfg.dt > 0.0 ? c->cfg.dt : 0.0;
   sp.cfl_num = c->cfl_num;
   sp.inv_det = c->inv_det;
@@ -127,6 +147,17 @@ dg_status launch_eval_t(dg_ctx* c, cudaStream_t s) {
 // Shu-Osher coefficients of SSP-RK1/2/3: w_{s+1} = a_s w_0 + b_s (w_s + dt R(w_s))
 const double RK_A[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.5, 0.0}, {0.0, 0.75, 1.0 / 3.0}};
 const double RK_B[3][3] = {{1.0, 0.0, 0.0}, {1.0, 0.5, 0.0}, {1.0, 0.25, 2.0 / 3.0}};
+// time of each stage's output state, in units of dt after the step start
+const double RK_C[3][3] = {{1.0, 0.0, 0.0}, {1.0, 1.0, 0.0}, {1.0, 0.5, 1.0}};
+
+// End of a time step: t += dt (fixed, or from the step's wave-speed slot);
+// the step's dt is kept in dt_out.  One thread, launched after the last stage
+// so that every stage reads a constant step time.
+__global__ void advance_time_kernel(double* t, double* dt_out, double dt_fixed, double cfl_num, const double* lam) {
+  const double dt = dt_fixed > 0.0 ? dt_fixed : cfl_num / lam[0];
+  *t += dt;
+  *dt_out = dt;
+}
 
 // Launch one full time step from eval parity ep, wave-speed slot lc.
 template <class Real>
@@ -147,12 +178,13 @@ dg_status launch_step_t(const dg_ctx* c, int ep, int lc, cudaStream_t s) {
     sp.vs_out = (Real*)c->vs[1 - pin];
     sp.rec_out = (Real*)c->rec[1 - pin];
     sp.lam = c->scal + lc;
-    if (st == S - 1) {
-      if (adaptive) sp.lam_next = c->scal + (1 - lc);
-      sp.t = c->scal + 2;
-    }
+    sp.c_eval = RK_C[S - 1][st];
+    if (st == S - 1 && adaptive) sp.lam_next = c->scal + (1 - lc);
     CK(launch_stage_any(c, MODE_STAGE, &sp, s));
   }
+  advance_time_kernel<<<1, 1, 0, s>>>(c->scal + 2, c->scal + 3, c->cfg.dt > 0.0 ? c->cfg.dt : 0.0, c->cfl_num,
+                                      c->scal + lc);
+  CK(cudaGetLastError());
   return DG_OK;
 }
 
@@ -257,11 +289,127 @@ void free_ctx(dg_ctx* c) {
     for (auto& g : row)
       if (g.exec) cudaGraphExecDestroy(g.exec);
   void* bufs[] = {c->w[0], c->w[1], c->w[2], c->vs[0], c->vs[1], c->rec[0], c->rec[1], c->hb, c->hbt,
-                  c->ghb, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec};
+                  c->ghb, c->lin, c->geo, c->vq, c->eq, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
+}
+
+// Per-element geometry of a general quad-split mesh from its vertices:
+// G = adj(B)^T, |det B|, 1/|det B|, outward unit normal and length of each
+// local edge (edge n runs from vertex n+1 to n+2), vertex a1; and the smallest
+// inscribed-circle diameter.  Rejects clockwise or degenerate triangles.
+dg_status build_geometry(const dg_config* cfg, std::vector<double>& geo, double* dmin) {
+  const int nx = cfg->nx, ny = cfg->ny;
+  const long long E = 2LL * nx * ny;
+  geo.assign((size_t)NGEO * E, 0.0);
+  const double* v = cfg->vertex_xy;
+  auto vx = [&](int i, int j) { return v[2 * ((size_t)j * (nx + 1) + i)]; };
+  auto vy = [&](int i, int j) { return v[2 * ((size_t)j * (nx + 1) + i) + 1]; };
+  double dm = 1e300;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      for (int t = 0; t < 2; ++t) {
+        const long long e = 2LL * ((long long)j * nx + i) + t;
+        double x[3], y[3];
+        if (t == 0) {
+          x[0] = vx(i, j); y[0] = vy(i, j);
+          x[1] = vx(i + 1, j); y[1] = vy(i + 1, j);
+          x[2] = vx(i, j + 1); y[2] = vy(i, j + 1);
+        } else {
+          x[0] = vx(i + 1, j + 1); y[0] = vy(i + 1, j + 1);
+          x[1] = vx(i, j + 1); y[1] = vy(i, j + 1);
+          x[2] = vx(i + 1, j); y[2] = vy(i + 1, j);
+        }
+        const double B11 = x[1] - x[0], B12 = x[2] - x[0], B21 = y[1] - y[0], B22 = y[2] - y[0];
+        const double det = B11 * B22 - B12 * B21;
+        if (!(det > 0.0) || !std::isfinite(det)) return DG_ERR_ARG;
+        geo[GEO_G11 * E + e] = B22;
+        geo[GEO_G12 * E + e] = -B21;
+        geo[GEO_G21 * E + e] = -B12;
+        geo[GEO_G22 * E + e] = B11;
+        geo[GEO_DET * E + e] = det;
+        geo[GEO_IDET * E + e] = 1.0 / det;
+        double per = 0.0;
+        for (int n = 0; n < 3; ++n) {
+          const int a = (n + 1) % 3, b = (n + 2) % 3;
+          const double tx = x[b] - x[a], ty = y[b] - y[a], len = std::hypot(tx, ty);
+          geo[(GEO_EDGE + 3 * n) * E + e] = ty / len;
+          geo[(GEO_EDGE + 3 * n + 1) * E + e] = -tx / len;
+          geo[(GEO_EDGE + 3 * n + 2) * E + e] = len;
+          per += len;
+        }
+        geo[GEO_A1X * E + e] = x[0];
+        geo[GEO_A1Y * E + e] = y[0];
+        dm = std::min(dm, 2.0 * det / per);
+      }
+  *dmin = dm;
+  return DG_OK;
+}
+
+// Gauss-Legendre nodes/weights on [0, 1] (Newton on P_n, three-term recurrence)
+void gauss01(int n, double* s, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 0.0;
+    for (int it = 0; it < 60; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-17) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      const double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    dp = n * (z * p1 - p0) / (z * z - 1.0);
+    s[i] = 0.5 * (1.0 + z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// Rules for the non-polynomial data of the §3.1 test: collapsed Gauss rule
+// on the triangle with ceil((3p+2)/2)+1 points per direction, Gauss rule on
+// edges with ceil((3p+1)/2)+1 points (the counts of the reference scheme's
+// exact-integration rules), edge rows carrying L_0..L_4 at each node.
+void build_rules(int p, std::vector<double>& vq, std::vector<double>& eq, int* nqv, int* nqe) {
+  const int nv = (3 * p + 3) / 2 + 1, ne = (3 * p + 2) / 2 + 1;
+  double s[16], w[16];
+  gauss01(nv, s, w);
+  *nqv = nv * nv;
+  vq.assign((size_t)3 * nv * nv, 0.0);
+  for (int a = 0; a < nv; ++a)
+    for (int b = 0; b < nv; ++b) {
+      const int q = a * nv + b;
+      vq[q] = s[a];
+      vq[nv * nv + q] = (1.0 - s[a]) * s[b];
+      vq[2 * nv * nv + q] = w[a] * w[b] * (1.0 - s[a]);
+    }
+  gauss01(ne, s, w);
+  *nqe = ne;
+  eq.assign((size_t)7 * ne, 0.0);
+  for (int q = 0; q < ne; ++q) {
+    const double z = 2.0 * s[q] - 1.0;
+    double pm = 1.0, pc = z;
+    eq[7 * q] = s[q];
+    eq[7 * q + 1] = w[q];
+    eq[7 * q + 2] = 1.0;
+    eq[7 * q + 3] = std::sqrt(3.0) * z;
+    for (int j = 1; j + 1 <= 4; ++j) {
+      const double pn = ((2 * j + 1) * z * pc - j * pm) / (j + 1);
+      pm = pc;
+      pc = pn;
+      eq[7 * q + 2 + j + 1] = std::sqrt(2.0 * (j + 1) + 1.0) * pn;
+    }
+  }
 }
 
 // Common part of dg_init / dg_init_device: d_fields = device FP64 SoA
@@ -283,17 +431,20 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   c->rsz = c->arith == ARITH_FP64 ? sizeof(double) : sizeof(float);
   c->stream = (cudaStream_t)stream;
   const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
-  c->mesh.nx = cfg->nx;
-  c->mesh.ny = cfg->ny;
-  c->mesh.E = c->E;
-  c->mesh.hx = hx;
-  c->mesh.hy = hy;
-  c->mesh.diag = std::hypot(hx, hy);
-  c->mesh.periodic = cfg->bc == DG_BC_PERIODIC;
+  c->mesh = make_mesh(cfg->nx, cfg->ny, cfg->x0, cfg->y0, cfg->Lx, cfg->Ly, cfg->bc == DG_BC_PERIODIC);
   c->det = hx * hy;
   c->inv_det = 1.0 / c->det;
   // smallest inscribed-circle diameter 4 area / perimeter (all triangles equal)
-  const double dmin = 4.0 * (0.5 * c->det) / (hx + hy + std::hypot(hx, hy));
+  double dmin = 4.0 * (0.5 * c->det) / (hx + hy + std::hypot(hx, hy));
+  std::vector<double> geo_h;
+  if (cfg->vertex_xy) {
+    dg_status gs = build_geometry(cfg, geo_h, &dmin);
+    if (gs != DG_OK) {
+      delete c;
+      return gs;
+    }
+  }
+  c->cfg.vertex_xy = nullptr;   // the caller's array is not kept
   c->cfl_num = cfg->cfl * dmin / (2.0 * cfg->p + 1.0);
   const long long E = c->E;
   const size_t st = (size_t)3 * c->K * E * c->rsz;
@@ -311,6 +462,14 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   alloc(&c->hb, (size_t)c->K * E * c->rsz);
   alloc(&c->hbt, (size_t)3 * c->P1 * E * c->rsz);
   alloc(&c->ghb, (size_t)2 * c->K1 * E * c->rsz);
+  if (c->arith == ARITH_FP64) alloc(&c->lin, (size_t)2 * c->K * c->K * E * c->rsz);
+  if (!geo_h.empty()) alloc((void**)&c->geo, sizeof(double) * geo_h.size());
+  std::vector<double> vq_h, eq_h;
+  if (cfg->forcing == DG_FORCING_MANUFACTURED) {
+    build_rules(cfg->p, vq_h, eq_h, &c->nqv, &c->nqe);
+    alloc((void**)&c->vq, sizeof(double) * vq_h.size());
+    alloc((void**)&c->eq, sizeof(double) * eq_h.size());
+  }
   alloc((void**)&c->scal, 4 * sizeof(double));
   alloc((void**)&c->err, sizeof(unsigned));
   alloc((void**)&c->partial, sizeof(double) * 2 * (size_t)((E + 127) / 128));
@@ -324,6 +483,12 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   }
   cudaStream_t ss = c->stream;
   cudaError_t ce = cudaMemsetAsync(c->scal, 0, 4 * sizeof(double), ss);
+  if (ce == cudaSuccess && c->geo) {
+    ce = cudaMemcpy(c->geo, geo_h.data(), sizeof(double) * geo_h.size(), cudaMemcpyHostToDevice);
+    c->mesh.geo = c->geo;
+  }
+  if (ce == cudaSuccess && c->vq) ce = cudaMemcpy(c->vq, vq_h.data(), sizeof(double) * vq_h.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess && c->eq) ce = cudaMemcpy(c->eq, eq_h.data(), sizeof(double) * eq_h.size(), cudaMemcpyHostToDevice);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(c->err, 0, sizeof(unsigned), ss);
   if (ce != cudaSuccess) {
     free_ctx(c);
@@ -338,9 +503,11 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   }
   cudaError_t le;
   switch (c->arith) {
-    case ARITH_FP64: le = static_fp64(c->P, c->mesh, d_hb, c->hb, c->hbt, c->ghb, ss); break;
-    case ARITH_FP32_P64: le = static_fp32p64(c->P, c->mesh, d_hb, c->hb, c->hbt, c->ghb, ss); break;
-    default: le = static_fp32p32(c->P, c->mesh, d_hb, c->hb, c->hbt, c->ghb, ss); break;
+    case ARITH_FP64: le = static_fp64(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, c->lin, ss); break;
+    case ARITH_FP32_P64:
+      le = static_fp32p64(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss);
+      break;
+    default: le = static_fp32p32(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss); break;
   }
   if (le == cudaSuccess) le = cudaStreamSynchronize(ss);
   if (le != cudaSuccess) {
@@ -465,18 +632,11 @@ dg_status dg_rk_step(dg_ctx* c, double* dt_used) {
   if (!c) return DG_ERR_ARG;
   dg_status s = ensure_evaluated(c);
   if (s != DG_OK) return s;
-  double dt = c->cfg.dt;
-  if (dt_used && !(c->cfg.dt > 0.0)) {
-    double lam = 0.0;
-    CK(cudaMemcpyAsync(&lam, c->scal + c->lc, sizeof lam, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    dt = c->cfl_num / lam;
-  }
   if ((s = launch_step(c, c->ep, c->lc, c->stream)) != DG_OK) return s;
   advance_parity(c);
   if (dt_used) {
+    CK(cudaMemcpyAsync(dt_used, c->scal + 3, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    *dt_used = dt;
   }
   return DG_OK;
 }

@@ -83,9 +83,13 @@ def test_rhs_matches_oracle_fp64(oracle_mod, p, bc):
     hb, xi, U, V = _state(o, wl)
     ref = o.rhs(hb, xi, U, V)
     got = _gpu_rhs(_cfg(wl), hb, xi, U, V)
+    # p = 4: the oracle builds the degree-4 functions by Gram-Schmidt in
+    # floating point (coefficients up to ~1e3, with cancellation), which adds
+    # ~1e-13 relative rounding; the FP64-path bar of 1e-12 applies there
+    tol = 1e-13 if p < 4 else 1e-12
     for f in range(3):
         scale = np.abs(ref[f]).max()
-        assert np.abs(got[f] - ref[f]).max() <= 1e-13 * scale, (f, np.abs(got[f] - ref[f]).max() / scale)
+        assert np.abs(got[f] - ref[f]).max() <= tol * scale, (f, np.abs(got[f] - ref[f]).max() / scale)
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])

@@ -54,7 +54,7 @@ def test_counts_and_status_strings(lib):
 def test_config_struct_layout(lib):
     from paper_1904_08684_gb300 import binding as B
     # int,int | 4 double | ptr | int(+pad) | double | 3 int(+pad) | 2 double | 2 int | 2 double
-    assert ctypes.sizeof(B.dg_config) == 120
+    assert ctypes.sizeof(B.dg_config) == 128
     assert B.dg_config.g.offset == 56 and B.dg_config.cfl.offset == 80 and B.dg_config.tau_bf.offset == 104
 
 
@@ -75,7 +75,7 @@ def test_invalid_configs_rejected_without_gpu(lib, bad):
 def test_unsupported_configs(lib):
     import numpy as np
     from paper_1904_08684_gb300 import binding as B
-    for kw in (dict(p=0), dict(bc="dirichlet")):
+    for kw in (dict(p=0), dict(bc="dirichlet"), dict(bc="periodic", vertex_xy=np.zeros((25, 2)))):
         base = dict(nx=4, ny=4, p=1, bc="periodic")
         base.update(kw)
         cfg = B.make_config(**base)
