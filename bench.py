@@ -63,6 +63,42 @@ FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max clock
 
 
+def _roofline(parts, precision, proj, launch_s, traffic):
+    """Roofline of the stage kernel.  parts: [(p, E)] of the instances of one
+    launch; launch_s: seconds per stage launch.  Algorithmic flops per
+    element and stage: 2 x the FMA counts of flops.SURVEY_FMA (velocity solve,
+    rest).  FP64 path: all flops against the FP64 rate; FP32 state with FP64
+    solve: the solve's flops against the FP64 rate (the pipe that binds),
+    with the FP32 share beside it; FP32 state with a double-float or FP32
+    solve: all flops against the FP32 rate."""
+    from paper_1904_08684_gb300 import flops as FL
+    fsolve = sum(2 * FL.SURVEY_FMA[p][0] * E for p, E in parts)
+    frest = sum(2 * FL.SURVEY_FMA[p][1] * E for p, E in parts)
+    word = 8 if precision == "fp64" else 4
+    alg_bytes = sum(FL.stage_bytes(p, word) * E for p, E in parts)
+    hbm_peak = _peaks().get("hbm_gbs")
+    fp64_src = "FP64 1.25 TFLOP/s nominal (recipe table)"
+    fp32_src = "FP32 152 SM x 128 lanes x 2 x 2.07 GHz"
+    if precision == "fp64":
+        ach, peak, src, what = (fsolve + frest) / launch_s / 1e12, FP64_PEAK_TFLOPS, fp64_src, "all flops (FP64)"
+    elif proj == "fp64":
+        ach, peak, src, what = (fsolve / launch_s / 1e12, FP64_PEAK_TFLOPS, fp64_src,
+                                "FP64 flops of the velocity solve")
+    else:
+        ach, peak, src, what = ((fsolve + frest) / launch_s / 1e12, FP32_PEAK_TFLOPS, fp32_src,
+                                "all flops on the FP32 pipe (the %s solve counted at its algorithmic flops)" % proj)
+    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic, "counted": what, "peak_source": src,
+            "flops_per_launch": fsolve + frest,
+            "hbm_algorithmic_bytes_per_launch": alg_bytes,
+            "hbm_achieved_gbs": alg_bytes / launch_s / 1e9,
+            "hbm_frac_of_measured": (alg_bytes / launch_s / 1e9) / hbm_peak if hbm_peak else None}
+    if precision != "fp64" and proj == "fp64":
+        roof["fp32_achieved_tflops"] = frest / launch_s / 1e12
+        roof["fp32_frac"] = frest / launch_s / 1e12 / FP32_PEAK_TFLOPS
+    return roof
+
+
 class ClockSampler:
     """nvidia-smi samples of the SM clock and throttle reasons (200 ms)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -178,6 +214,13 @@ def _setup_device_inputs(B, torch, wl, cfg, stream):
     return coef[0], coef[1], zero, zero
 
 
+def _dtype(precision, proj):
+    """arithmetic of the path: state/contractions, plus the velocity solve"""
+    if precision == "fp64":
+        return "f64"
+    return {"fp64": "f32+f64solve", "fp32": "f32", "df64": "f32+df64solve"}[proj]
+
+
 def _cfg_of(B, wl, args):
     return B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc, precision=wl.precision, rk_order=wl.rk_order,
                          cfl=wl.cfl, dt=wl.dt, g=wl.g, x0=wl.x0, y0=wl.y0, Lx=wl.Lx, Ly=wl.Ly,
@@ -235,28 +278,12 @@ def run_batch(args, wls):
     finally:
         B.dg_batch_destroy(b)
     launch_s = step_ms * 1e-3 / S
-    fp64 = wls[0].precision == "fp64"
-    word = 8 if fp64 else 4
-    f64 = sum(2 * FL.SURVEY_FMA[wl.p][0] * wl.E for wl in wls)
-    frest = sum(2 * FL.SURVEY_FMA[wl.p][1] * wl.E for wl in wls)
-    peaks = _peaks()
-    hbm_peak = peaks.get("hbm_gbs")
-    alg_bytes = sum(FL.stage_bytes(wl.p, word) * wl.E for wl in wls)
-    if fp64:
-        ach, peak, what = (f64 + frest) / launch_s / 1e12, FP64_PEAK_TFLOPS, "all FP64 flops"
-    else:
-        ach, peak, what = f64 / launch_s / 1e12, FP64_PEAK_TFLOPS, "FP64 flops of the velocity solve"
-    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-            "traffic": _measured_traffic("ensemble-256" if not fp64 else "ensemble-256-fp64", FL.source_hash()),
-            "counted": what, "peak_source": "FP64 1.25 TFLOP/s nominal (recipe table)",
-            "fp32_achieved_tflops": None if fp64 else frest / launch_s / 1e12,
-            "fp32_frac": None if fp64 else frest / launch_s / 1e12 / FP32_PEAK_TFLOPS,
-            "hbm_achieved_gbs": alg_bytes / launch_s / 1e9,
-            "hbm_frac_of_measured": (alg_bytes / launch_s / 1e9) / hbm_peak if hbm_peak else None}
+    roof = _roofline([(wl.p, wl.E) for wl in wls], wls[0].precision, args.proj, launch_s,
+                     _measured_traffic("ensemble-256-" + wls[0].precision + "-" + args.proj, FL.source_hash()))
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if fp64 else ("f32+f64solve" if args.proj == "fp64" else "f32"),
+           "dtype": _dtype(wls[0].precision, args.proj),
            "data": "synthetic (seeded SplitMix64 fields, projected on device)",
            "config": {"workload": "ensemble-%d" % len(wls), "instances": len(wls),
                       "elements": sum(wl.E for wl in wls),
@@ -266,7 +293,7 @@ def run_batch(args, wls):
                                                                zip((32, 64, 96, 128), tune_ms)},
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
-           "gpu_launches": S * args.steps, "roofline": roof,
+           "gpu_launches": S * args.steps, "roofline": roof,   # one persistent launch per stage
            "e2e": {"value": dofs * S / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
            "clocks": clk.summary(), "sim_time_range": [float(min(tvals)), float(max(tvals))]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -319,45 +346,35 @@ def run_ours(args):
         # state goes host -> device (dg_set_state), one dg_run step, and the
         # state comes back (dg_get_state)
         E, K = wl.E, wl.K
-        st = B.dg_get_state(ctx, E, K)
-        host = [torch.from_numpy(a).pin_memory().numpy() for a in st]
+        host = [torch.empty((E, K), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+        B.dg_get_state(ctx, E, K, out=host)
         n_e2e = max(1, min(args.steps, args.e2e_steps))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
             B.dg_set_state(ctx, *host, t=0.0)
             B.dg_run(ctx, 1)
-            host = B.dg_get_state(ctx, E, K)
+            B.dg_get_state(ctx, E, K, out=host)
         e2e_s = (time.perf_counter() - t0) / n_e2e
     finally:
         B.dg_destroy(ctx)
-    # roofline of the stage kernel (the only kernel of the timed graphs)
+    # roofline of the stage kernel (the only kernel of the timed graphs but
+    # for the one-thread time advance)
     launch_s = step_ms * 1e-3 / S
-    fp64 = wl.precision == "fp64"
-    word = 8 if fp64 else 4
-    flop = FL.algorithmic_flops(wl.p) * wl.E
-    peaks = _peaks()
-    hbm_peak = peaks.get("hbm_gbs")
-    alg_bytes = FL.stage_bytes(wl.p, word) * wl.E
-    roof = {"bound": "alu", "achieved": flop / launch_s / 1e12,
-            "peak": FP64_PEAK_TFLOPS if fp64 else FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "traffic": _measured_traffic(wl.name, FL.source_hash()),
-            "peak_source": ("FP64 1.25 TFLOP/s nominal (recipe table)" if fp64 else
-                            "FP32 152 SM x 128 lanes x 2 x 2.07 GHz"),
-            "flops_per_element_stage": FL.algorithmic_flops(wl.p),
-            "hbm_achieved_gbs": alg_bytes / launch_s / 1e9,
-            "hbm_frac_of_measured": (alg_bytes / launch_s / 1e9) / hbm_peak if hbm_peak else None}
-    roof["frac"] = roof["achieved"] / roof["peak"]
+    traffic_key = wl.name if wl.precision == "fp64" else wl.name + "-" + args.proj
+    roof = _roofline([(wl.p, wl.E)], wl.precision, args.proj, launch_s,
+                     _measured_traffic(traffic_key, FL.source_hash()))
     e2e_val = dof_stage * S / e2e_s
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64" if fp64 else ("f32+f64solve" if args.proj == "fp64" else "f32"),
+           "vs_baseline": None, "dtype": _dtype(wl.precision, args.proj),
            "data": "synthetic (seeded SplitMix64 fields, projected on device)",
            "config": {"workload": wl.name, "elements": wl.E, "p": wl.p, "K": wl.K, "rk_stages": S,
                       "dof_per_stage": dof_stage, "precision": wl.precision, "bc": wl.bc,
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
-           "gpu_launches": S * args.steps,
+           # per step: S stage kernels and the one-thread time-advance kernel
+           "gpu_launches": (S + 1) * args.steps,
            "roofline": roof,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * wl.K * wl.E * 8,
                    "d2h_bytes_per_step": 3 * wl.K * wl.E * 8},
@@ -371,15 +388,14 @@ def run_ours(args):
         print(json.dumps(out))
 
 
-def cpu_baseline(wl, seconds):
-    """The FP64 oracle, as it stands, on the host cores: right-hand sides of a
-    contiguous block of elements (1/16 of the mesh) of the same workload,
-    repeated for about ``seconds``; one RHS evaluation is one RK stage."""
+def _oracle_sample(wl):
+    """The FP64 oracle on a contiguous block of elements (1/16 of the mesh) of
+    the workload, with the fields projected where the block and its
+    neighbours need them."""
     import oracle
     o = oracle.Oracle(wl.nx, wl.ny, wl.p, bc=wl.bc, rk_order=wl.rk_order, cfl=wl.cfl, Lx=wl.Lx, Ly=wl.Ly)
     nsamp = max(1, o.E // 16)
     elems = np.arange(nsamp, dtype=np.int32)
-    # fields only where the sample and its neighbours need them
     _, _, nb = o.geometry()
     need = np.zeros(o.E, bool)
     need[elems] = True
@@ -391,7 +407,13 @@ def cpu_baseline(wl, seconds):
     vals_xi[need] = wl.xi0(xy[need][..., 0], xy[need][..., 1])
     hb = o.project_hb_values(vals_hb)
     xi = o.project_values(vals_xi)
-    z = np.zeros_like(xi)
+    return o, hb, xi, np.zeros_like(xi), elems
+
+
+def _time_sample(sample, seconds):
+    """repeat the oracle's RHS of the sample (one RK stage of those elements)
+    for about ``seconds``; returns (updated DOFs, elapsed s, repetitions)"""
+    o, hb, xi, z, elems = sample
     reps, t0 = 0, time.perf_counter()
     while True:
         o.rhs(hb, xi, z, z, elems=elems)
@@ -399,33 +421,54 @@ def cpu_baseline(wl, seconds):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    rate = 3 * wl.K * nsamp * reps / el
-    return {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return 3 * o.K * len(elems) * reps, el, reps
+
+
+def cpu_baseline(wl, seconds):
+    """The FP64 oracle, as it stands, on the host cores: right-hand sides of a
+    contiguous block of elements (1/16 of the mesh) of the same workload,
+    repeated for about ``seconds``; one RHS evaluation is one RK stage."""
+    sample = _oracle_sample(wl)
+    dofs, el, reps = _time_sample(sample, seconds)
+    return {"value": dofs / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
             "sample": "oracle RHS (one RK stage) of elements 0..%d of %s, %d repetitions, %.1f s"
-                      % (nsamp - 1, wl.name, reps, el)}
+                      % (len(sample[4]) - 1, wl.name, reps, el)}
 
 
 def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    wl = WORKLOADS[args.workload]()
-    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    wls = WORKLOADS[args.workload]()
+    if isinstance(wls, list):                     # ensemble: one instance per order
+        wls = [next(w for w in wls if w.p == q) for q in (1, 2, 3) if any(w.p == q for w in wls)]
+    else:
+        wls = [wls]
+    samples = [_oracle_sample(w) for w in wls]
+    per_step = max(0.5, args.cpu_seconds / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_baseline(wl, per_step)
-    t0 = time.perf_counter()
-    rates = [cpu_baseline(wl, per_step) for _ in range(args.steps)]
-    el = time.perf_counter() - t0
-    value = statistics.mean(r["value"] for r in rates)
-    cb = dict(rates[-1])
-    cb["value"] = value
+        for sm in samples:
+            _time_sample(sm, per_step / len(samples))
+    dofs = el = 0.0
+    reps = 0
+    for _ in range(args.steps):
+        for sm in samples:
+            d, e, r = _time_sample(sm, per_step / len(samples))
+            dofs += d
+            el += e
+            reps += r
+    value = dofs / el
+    wl = wls[0]
+    sample = "oracle RHS (one RK stage) of 1/16 of the elements of %s, %d evaluations in %.1f s" % (
+        ", ".join(w.name for w in wls), reps, el)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded SplitMix64 fields)",
-           "config": {"workload": wl.name, "elements": wl.E, "p": wl.p, "K": wl.K,
+           "config": {"workload": args.workload, "elements": wl.E, "p": wl.p, "K": wl.K,
                       "rk_stages": wl.rk_order, "precision": "fp64", "bc": wl.bc},
-           "cpu_baseline": cb,
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -433,11 +476,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="waves-p2-512", choices=sorted(WORKLOADS))
-    ap.add_argument("--proj", default="fp64", choices=["fp64", "fp32"],
+    ap.add_argument("--proj", default="fp64", choices=["fp64", "fp32", "df64"],
                     help="velocity-solve arithmetic of the FP32 state path")
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -66,7 +66,10 @@ typedef enum {
 
 typedef enum { DG_BC_PERIODIC = 0, DG_BC_REFLECTIVE = 1, DG_BC_DIRICHLET = 2 } dg_bc;
 typedef enum { DG_PREC_FP64 = 0, DG_PREC_FP32_MIXED = 1 } dg_precision;
-typedef enum { DG_PROJ_FP64 = 0, DG_PROJ_FP32 = 1 } dg_proj_precision;
+/* Arithmetic of the velocity solve of DG_PREC_FP32_MIXED: FP64 (default), FP32,
+ * or double-float (pairs of FP32 numbers, ~48 significant bits, on the FP32
+ * units; p <= 3, uniform meshes without forcing only). */
+typedef enum { DG_PROJ_FP64 = 0, DG_PROJ_FP32 = 1, DG_PROJ_DF64 = 2 } dg_proj_precision;
 /* §3.1 convergence test of the paper: xi = 2.3 - 0.4 S, U = 0.6 + 0.04 S,
  * V = 0.3 + 0.04 S, S = sin(pi (x + y + 0.2 t) / 600), on the bathymetry
  * h_b = 1 + x/1000 + 2 y/1000 (which the caller projects), with the body force

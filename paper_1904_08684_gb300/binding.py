@@ -16,7 +16,8 @@ from . import build as _build
 DG_OK, DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_DRY, DG_ERR_NONFINITE, DG_ERR_TIMEOUT = range(8)
 DG_BC_PERIODIC, DG_BC_REFLECTIVE, DG_BC_DIRICHLET = 0, 1, 2
 DG_PREC_FP64, DG_PREC_FP32_MIXED = 0, 1
-DG_PROJ_FP64, DG_PROJ_FP32 = 0, 1
+DG_PROJ_FP64, DG_PROJ_FP32, DG_PROJ_DF64 = 0, 1, 2
+PROJ = {"fp64": DG_PROJ_FP64, "fp32": DG_PROJ_FP32, "df64": DG_PROJ_DF64}
 
 BC = {"periodic": DG_BC_PERIODIC, "reflective": DG_BC_REFLECTIVE, "dirichlet": DG_BC_DIRICHLET}
 PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
@@ -58,7 +59,7 @@ def make_config(nx, ny, p, bc="periodic", precision="fp64", rk_order=3, cfl=0.2,
                      BC[bc] if isinstance(bc, str) else int(bc),
                      PREC[precision] if isinstance(precision, str) else int(precision),
                      rk_order, cfl, dt,
-                     DG_PROJ_FP32 if proj_precision == "fp32" else DG_PROJ_FP64, block_size,
+                     PROJ[proj_precision] if isinstance(proj_precision, str) else int(proj_precision), block_size,
                      float(tau_bf), float(f_c), int(forcing))
     if vertex_xy is not None:
         cfg._vertex_keep = _keep   # keep the vertex array alive with the struct
@@ -204,8 +205,14 @@ def dg_run(ctx, nsteps):
     return t.value
 
 
-def dg_get_state(ctx, E, K):
-    out = [np.zeros((E, K)) for _ in range(3)]
+def dg_get_state(ctx, E, K, out=None):
+    """state as three host (E, K) FP64 arrays (written into ``out`` if given,
+    e.g. page-locked buffers)"""
+    if out is None:
+        out = [np.zeros((E, K)) for _ in range(3)]
+    for a in out:
+        if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != E * K:
+            raise ValueError("out arrays must be contiguous float64 of %d x %d" % (E, K))
     _check(load().dg_get_state(ctx, *[_hptr(a) for a in out]), "dg_get_state")
     return out
 

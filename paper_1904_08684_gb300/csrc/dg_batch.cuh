@@ -49,7 +49,7 @@ struct BatchArgs {
 };
 
 template <class Real, class PR, int MODE>
-__global__ void __launch_bounds__(128) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(128, (stage_min_blocks<3, Real>())) batch_kernel(const BatchArgs a) {
   __shared__ int s_item;
   for (;;) {
     __syncthreads();
@@ -128,29 +128,20 @@ __global__ void __launch_bounds__(128) batch_kernel(const BatchArgs a) {
   }
 }
 
-cudaError_t batch_launch_fp64(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s);
-cudaError_t batch_launch_fp32p64(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s);
-cudaError_t batch_launch_fp32p32(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s);
-cudaError_t batch_occupancy_fp64(int block, int* blocks_per_sm);
-cudaError_t batch_occupancy_fp32p64(int block, int* blocks_per_sm);
-cudaError_t batch_occupancy_fp32p32(int block, int* blocks_per_sm);
-
-#define DGSWE_DEFINE_BATCH(SUFFIX, REAL, PREAL)                                                       \
-  cudaError_t batch_launch_##SUFFIX(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s) { \
-    if (mode == MODE_EVAL)                                                                            \
-      batch_kernel<REAL, PREAL, MODE_EVAL><<<grid, block, 0, s>>>(a);                                 \
-    else                                                                                              \
-      batch_kernel<REAL, PREAL, MODE_STAGE><<<grid, block, 0, s>>>(a);                                \
-    return cudaGetLastError();                                                                        \
-  }                                                                                                   \
-  cudaError_t batch_occupancy_##SUFFIX(int block, int* blocks_per_sm) {                               \
-    int a = 0, b = 0;                                                                                 \
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                    \
-        &a, batch_kernel<REAL, PREAL, MODE_STAGE>, block, 0);                                         \
-    if (e != cudaSuccess) return e;                                                                   \
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_kernel<REAL, PREAL, MODE_EVAL>, block, 0); \
-    *blocks_per_sm = a < b ? a : b;                                                                   \
-    return e;                                                                                         \
-  }
+// Launch and occupancy of one (arithmetic, mode) instantiation; each is
+// compiled separately from dg_batch_inst.cu (build flags select it), and the
+// per-arithmetic dispatchers batch_launch_<suffix>(mode, ...) and
+// batch_occupancy_<suffix> live in dg_dispatch.cu.
+#define DGSWE_BATCH_DECLARE(SUFFIX)                                                                  \
+  cudaError_t batch_launch_##SUFFIX##_m0(int grid, int block, const BatchArgs& a, cudaStream_t s);  \
+  cudaError_t batch_launch_##SUFFIX##_m1(int grid, int block, const BatchArgs& a, cudaStream_t s);  \
+  cudaError_t batch_occupancy_##SUFFIX##_m0(int block, int* blocks_per_sm);                         \
+  cudaError_t batch_occupancy_##SUFFIX##_m1(int block, int* blocks_per_sm);                         \
+  cudaError_t batch_launch_##SUFFIX(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s); \
+  cudaError_t batch_occupancy_##SUFFIX(int block, int* blocks_per_sm);
+DGSWE_BATCH_DECLARE(fp64)
+DGSWE_BATCH_DECLARE(fp32p64)
+DGSWE_BATCH_DECLARE(fp32p32)
+DGSWE_BATCH_DECLARE(fp32pdf)
 
 }  // namespace dgswe

@@ -79,6 +79,7 @@ cudaError_t launch_batch(const dg_batch* b, int mode, const BatchArgs& a, cudaSt
   switch (b->arith) {
     case ARITH_FP64: return batch_launch_fp64(mode, b->grid, b->block, a, s);
     case ARITH_FP32_P64: return batch_launch_fp32p64(mode, b->grid, b->block, a, s);
+    case ARITH_FP32_PDF: return batch_launch_fp32pdf(mode, b->grid, b->block, a, s);
     default: return batch_launch_fp32p32(mode, b->grid, b->block, a, s);
   }
 }
@@ -170,6 +171,7 @@ dg_status build_items(dg_batch* b, int block) {
   switch (b->arith) {
     case ARITH_FP64: e = batch_occupancy_fp64(block, &occ); break;
     case ARITH_FP32_P64: e = batch_occupancy_fp32p64(block, &occ); break;
+    case ARITH_FP32_PDF: e = batch_occupancy_fp32pdf(block, &occ); break;
     default: e = batch_occupancy_fp32p32(block, &occ); break;
   }
   CK(e);
@@ -243,7 +245,8 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   b->n = n;
   b->arith = cfgs[0].precision == DG_PREC_FP64
                  ? ARITH_FP64
-                 : (cfgs[0].proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32 : ARITH_FP32_P64);
+                 : (cfgs[0].proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32
+                    : cfgs[0].proj_precision == DG_PROJ_DF64 ? ARITH_FP32_PDF : ARITH_FP32_P64);
   b->rsz = b->arith == ARITH_FP64 ? 8 : 4;
   b->S = cfgs[0].rk_order;
   b->adaptive = !(cfgs[0].dt > 0.0);
@@ -345,6 +348,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     switch (b->arith) {
       case ARITH_FP64: e = static_fp64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, pl, s); break;
       case ARITH_FP32_P64: e = static_fp32p64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
+      case ARITH_FP32_PDF: e = static_fp32pdf(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
       default: e = static_fp32p32(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
     }
   }

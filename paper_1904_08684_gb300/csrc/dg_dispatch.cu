@@ -1,0 +1,87 @@
+// Order (and mode) dispatch of the separately compiled launchers:
+// stage_<suffix>(p, ...) calls stage_<suffix>_p<p> (dg_stage_inst.cu),
+// static_/diag_<suffix>(p, ...) call *_p<p> (dg_aux_inst.cu) and
+// batch_launch_<suffix>(mode, ...) calls batch_launch_<suffix>_m<mode>
+// (dg_batch_inst.cu).  Orders outside 1..4 return cudaErrorInvalidValue.
+#include "dg_batch.cuh"
+#include "dg_launch.cuh"
+
+namespace dgswe {
+
+#define DGSWE_DISPATCH(SUFFIX)                                                                  \
+  cudaError_t stage_##SUFFIX(int p, int mode, int block, const void* params, cudaStream_t s) {         \
+    switch (p) {                                                                                      \
+      case 1: return stage_##SUFFIX##_p1(mode, block, params, s);                                      \
+      case 2: return stage_##SUFFIX##_p2(mode, block, params, s);                                      \
+      case 3: return stage_##SUFFIX##_p3(mode, block, params, s);                                      \
+      case 4: return stage_##SUFFIX##_p4(mode, block, params, s);                                      \
+    }                                                                                                 \
+    return cudaErrorInvalidValue;                                                                     \
+  }
+
+DGSWE_DISPATCH(fp64)
+DGSWE_DISPATCH(fp32p64)
+DGSWE_DISPATCH(fp32p32)
+DGSWE_DISPATCH(fp64_gen)
+DGSWE_DISPATCH(fp32p64_gen)
+DGSWE_DISPATCH(fp32p32_gen)
+DGSWE_DISPATCH(fp32pdf)
+
+// the double-float velocity solve is built for p <= 3: its p = 4 entries
+// reject the call
+cudaError_t stage_fp32pdf_p4(int, int, const void*, cudaStream_t) { return cudaErrorInvalidValue; }
+cudaError_t static_fp32pdf_p4(const Mesh&, double, const double*, void*, void*, void*, void*, cudaStream_t) {
+  return cudaErrorInvalidValue;
+}
+cudaError_t diag_fp32pdf_p4(const Mesh&, const void*, const void*, double, double, double*, cudaStream_t) {
+  return cudaErrorInvalidValue;
+}
+
+#define DGSWE_BATCH_DISPATCH(SUFFIX)                                                                  \
+  cudaError_t batch_launch_##SUFFIX(int mode, int grid, int block, const BatchArgs& a, cudaStream_t s) { \
+    return mode == MODE_EVAL ? batch_launch_##SUFFIX##_m0(grid, block, a, s)                           \
+                             : batch_launch_##SUFFIX##_m1(grid, block, a, s);                          \
+  }                                                                                                   \
+  cudaError_t batch_occupancy_##SUFFIX(int block, int* blocks_per_sm) {                               \
+    int a = 0, b = 0;                                                                                 \
+    cudaError_t e = batch_occupancy_##SUFFIX##_m0(block, &a);                                         \
+    if (e == cudaSuccess) e = batch_occupancy_##SUFFIX##_m1(block, &b);                               \
+    *blocks_per_sm = a < b ? a : b;                                                                   \
+    return e;                                                                                         \
+  }
+
+#define DGSWE_AUX_DISPATCH(SUFFIX)                                                                     \
+  cudaError_t static_##SUFFIX(int p, const Mesh& m, double gg, const double* hb64, void* hb, void* hbt,         \
+                              void* ghb, void* lin, cudaStream_t s) {                                           \
+    switch (p) {                                                                                                \
+      case 1: return static_##SUFFIX##_p1(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
+      case 2: return static_##SUFFIX##_p2(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
+      case 3: return static_##SUFFIX##_p3(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
+      case 4: return static_##SUFFIX##_p4(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
+    }                                                                                                           \
+    return cudaErrorInvalidValue;                                                                               \
+  }                                                                                                             \
+  cudaError_t diag_##SUFFIX(int p, const Mesh& m, const void* w, const void* hb, double det, double gg,         \
+                            double* partial, cudaStream_t s) {                                                  \
+    switch (p) {                                                                                                \
+      case 1: return diag_##SUFFIX##_p1(m, w, hb, det, gg, partial, s);                                         \
+      case 2: return diag_##SUFFIX##_p2(m, w, hb, det, gg, partial, s);                                         \
+      case 3: return diag_##SUFFIX##_p3(m, w, hb, det, gg, partial, s);                                         \
+      case 4: return diag_##SUFFIX##_p4(m, w, hb, det, gg, partial, s);                                         \
+    }                                                                                                           \
+    return cudaErrorInvalidValue;                                                                               \
+  }
+
+// set-up and diagnostics
+DGSWE_AUX_DISPATCH(fp64)
+DGSWE_AUX_DISPATCH(fp32p64)
+DGSWE_AUX_DISPATCH(fp32p32)
+DGSWE_AUX_DISPATCH(fp32pdf)
+
+// batched persistent kernel: mode 0 = evaluation, 1 = stage
+DGSWE_BATCH_DISPATCH(fp64)
+DGSWE_BATCH_DISPATCH(fp32p64)
+DGSWE_BATCH_DISPATCH(fp32p32)
+DGSWE_BATCH_DISPATCH(fp32pdf)
+
+}  // namespace dgswe

@@ -389,6 +389,60 @@ __device__ __forceinline__ R edge_point(const R* tau) {
 }
 
 // ---------------------------------------------------------------------------
+// Double-float arithmetic ("df64") on the FP32 pipe: a value is hi + lo with
+// |lo| <= ulp(hi)/2 (about 48 significant bits).  Built from the error-free
+// transformations of Knuth (two-sum) and Dekker (two-product, here with a
+// fused multiply-add), with the accurate double-double addition of
+// Hida, Li and Bailey.  Explicit _rn intrinsics keep the compiler from
+// contracting or reassociating the steps.
+struct df64 {
+  float hi, lo;
+  __host__ __device__ constexpr df64() : hi(0.f), lo(0.f) {}
+  __host__ __device__ constexpr df64(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr explicit df64(int a) : hi(float(a)), lo(0.f) {}
+  __host__ __device__ constexpr explicit df64(float a) : hi(a), lo(0.f) {}
+  // split of a double (used on compile-time constants only)
+  __host__ __device__ constexpr explicit df64(double a) : hi(float(a)), lo(float(a - double(float(a)))) {}
+  __device__ explicit operator float() const { return __fadd_rn(hi, lo); }
+  __device__ explicit operator double() const { return double(hi) + double(lo); }
+};
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return df64(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb)));
+}
+__device__ __forceinline__ df64 df_quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df64(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ df64 operator+(df64 a, df64 b) {
+  df64 s = df_two_sum(a.hi, b.hi);
+  const df64 t = df_two_sum(a.lo, b.lo);
+  s = df_quick_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_quick_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ df64 operator-(df64 a) { return df64(-a.hi, -a.lo); }
+__device__ __forceinline__ df64 operator-(df64 a, df64 b) { return a + (-b); }
+__device__ __forceinline__ df64 operator*(df64 a, df64 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_quick_two_sum(p, e);
+}
+__device__ __forceinline__ df64 operator/(df64 a, df64 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const df64 r = a - b * df64(q1);
+  return df_quick_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+__device__ __forceinline__ bool operator>(df64 a, df64 b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+// a * b + c in the arithmetic of the velocity solve (float, double, df64)
+__device__ __forceinline__ double mad(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df64 mad(df64 a, df64 b, df64 c) { return a * b + c; }
+
+// ---------------------------------------------------------------------------
 // Velocity projection (Eq. (12)): A u = U, A v = V with
 // A_ab = sum_n T[n][a][b] H_n (SPD iff H > 0 on the element), solved by an
 // LDL^T factorisation in precision PR.  Returns false if a pivot is not
@@ -407,11 +461,11 @@ __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R
     PR d = PR(0);
     sfor<0, K>([&](auto n) {
       constexpr double t = Tb::T[CV(n)][j][j];
-      if constexpr (t != 0.0) d = fma(PR(t), Hd[CV(n)], d);
+      if constexpr (t != 0.0) d = mad(PR(t), Hd[CV(n)], d);
     });
     sfor<0, j>([&](auto k) {
       W[CV(k)] = L[j][CV(k)] * Dg[CV(k)];
-      d = fma(-L[j][CV(k)], W[CV(k)], d);
+      d = mad(-L[j][CV(k)], W[CV(k)], d);
     });
     ok = ok && (d > PR(0));
     Dg[j] = d;
@@ -421,9 +475,9 @@ __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R
       PR a = PR(0);
       sfor<0, K>([&](auto n) {
         constexpr double t = Tb::T[CV(n)][i][j];
-        if constexpr (t != 0.0) a = fma(PR(t), Hd[CV(n)], a);
+        if constexpr (t != 0.0) a = mad(PR(t), Hd[CV(n)], a);
       });
-      sfor<0, j>([&](auto k) { a = fma(-L[i][CV(k)], W[CV(k)], a); });
+      sfor<0, j>([&](auto k) { a = mad(-L[i][CV(k)], W[CV(k)], a); });
       L[i][j] = a * rD[j];
     });
   });
@@ -432,13 +486,13 @@ __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R
     sfor<0, K>([&](auto ii) {
       constexpr int i = CV(ii);
       PR s = PR(b[i]);
-      sfor<0, i>([&](auto k) { s = fma(-L[i][CV(k)], y[CV(k)], s); });
+      sfor<0, i>([&](auto k) { s = mad(-L[i][CV(k)], y[CV(k)], s); });
       y[i] = s;
     });
     sfor<0, K>([&](auto rr) {
       constexpr int i = K - 1 - CV(rr);
       PR s = y[i] * rD[i];
-      sfor<i + 1, K>([&](auto k) { s = fma(-L[CV(k)][i], y[CV(k)], s); });
+      sfor<i + 1, K>([&](auto k) { s = mad(-L[CV(k)][i], y[CV(k)], s); });
       y[i] = s;
       x[i] = R(s);
     });
@@ -462,7 +516,7 @@ __device__ __forceinline__ void basis_at(double xr, double yr, double* phi) {
     sfor<0, 5>([&](auto a) {
       sfor<0, 5 - CV(a)>([&](auto b) {
         constexpr double c = BasisMonomials::c[CV(i)][CV(a)][CV(b)];
-        if constexpr (c != 0.0) v = fma(c, xp[CV(a)] * yp[CV(b)], v);
+        if constexpr (c != 0.0) v = mad(c, xp[CV(a)] * yp[CV(b)], v);
       });
     });
     phi[CV(i)] = v;
@@ -956,8 +1010,17 @@ __device__ __forceinline__ double block_max(double v) {
 // per right-hand side (MODE_RHS).  One thread per element.  FEAT = 0 is the
 // uniform-mesh path; FEAT = 1 adds general meshes, the §3.1 body force and
 // Dirichlet edges (kept out of the fast path's registers and code).
+// Minimum resident 128-thread blocks per SM requested from the register
+// allocator (measured on GB300): FP32-state kernels run fastest at 4 (<= 128
+// registers, spilling a little), FP64 at p <= 2 at 3 (their natural fit);
+// FP64 at p >= 3 needs the full register file.
+template <int P, class Real>
+constexpr int stage_min_blocks() {
+  return std::is_same<Real, float>::value ? 4 : (P <= 2 ? 3 : 1);
+}
+
 template <int P, class Real, class PR, int MODE, int FEAT>
-__global__ void __launch_bounds__(128) stage_kernel(const StageParams<Real> sp) {
+__global__ void __launch_bounds__(128, (stage_min_blocks<P, Real>())) stage_kernel(const StageParams<Real> sp) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   double lam_e = 0.0;
   unsigned err = 0;

@@ -1,5 +1,5 @@
-// dg_launch.cuh -- launch entry points shared by the per-precision
-// translation units (each one instantiates the kernels for one arithmetic).
+// dg_launch.cuh -- launch entry points of the stage, set-up and diagnostics
+// kernels, shared by the instantiation units and the host API.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -11,75 +11,85 @@
 namespace dgswe {
 
 // arithmetic of one context: state/contractions and velocity solve
-enum Arith { ARITH_FP64 = 0, ARITH_FP32_P64 = 1, ARITH_FP32_P32 = 2 };
+enum Arith { ARITH_FP64 = 0, ARITH_FP32_P64 = 1, ARITH_FP32_P32 = 2, ARITH_FP32_PDF = 3 };
 
-// Launch one stage_kernel.  params points to a StageParams<double> (FP64) or
-// StageParams<float>.  Returns the launch error.
-cudaError_t launch_diag(int arith, int p, const Mesh& m, const void* w, const void* hb, double det, double g,
-                        double* partial, cudaStream_t s);
+// Stage launchers.  Each (arithmetic, feature set, order) combination is
+// compiled separately from dg_stage_inst.cu (build flags select it), so the
+// build runs many small compilations in parallel; the per-arithmetic
+// dispatchers stage_<suffix>(p, ...) live in dg_dispatch.cu.
+#define DGSWE_PASTE4(a, b, c, d) a##b##c##d
+#define DGSWE_STAGE_NAME(SUFFIX, P) DGSWE_PASTE4(stage_, SUFFIX, _p, P)
+#define DGSWE_DECLARE_STAGE_P(SUFFIX, P) \
+  cudaError_t DGSWE_STAGE_NAME(SUFFIX, P)(int mode, int block, const void* params, cudaStream_t s);
 
-template <class Real>
-inline long long grid_for(long long E, int block) {
-  return (E + block - 1) / block;
+template <int P, class REAL, class PREAL, int FEAT, int MODE>
+cudaError_t launch_stage_pm(int block, const void* params, cudaStream_t s) {
+  const StageParams<REAL>& sp = *static_cast<const StageParams<REAL>*>(params);
+  const long long g = (sp.m.E + block - 1) / block;
+  stage_kernel<P, REAL, PREAL, MODE, FEAT><<<(unsigned)g, block, 0, s>>>(sp);
+  return cudaGetLastError();
 }
 
-// stage launchers of one arithmetic and feature set (one translation unit each)
-#define DGSWE_DEFINE_STAGE(SUFFIX, REAL, PREAL, FEAT)                                                     \
-  template <int P, int MODE>                                                                               \
-  static cudaError_t stage_##SUFFIX##_pm(int block, const void* params, cudaStream_t s) {                  \
-    const StageParams<REAL>& sp = *static_cast<const StageParams<REAL>*>(params);                          \
-    const long long g = (sp.m.E + block - 1) / block;                                                      \
-    stage_kernel<P, REAL, PREAL, MODE, FEAT><<<(unsigned)g, block, 0, s>>>(sp);                            \
-    return cudaGetLastError();                                                                             \
-  }                                                                                                        \
-  template <int P>                                                                                         \
-  static cudaError_t stage_##SUFFIX##_p(int mode, int block, const void* params, cudaStream_t s) {         \
-    if (mode == MODE_EVAL) return stage_##SUFFIX##_pm<P, MODE_EVAL>(block, params, s);                     \
-    if (mode == MODE_STAGE) return stage_##SUFFIX##_pm<P, MODE_STAGE>(block, params, s);                   \
-    return stage_##SUFFIX##_pm<P, MODE_RHS>(block, params, s);                                             \
-  }                                                                                                        \
-  cudaError_t stage_##SUFFIX(int p, int mode, int block, const void* params, cudaStream_t s) {             \
-    switch (p) {                                                                                           \
-      case 1: return stage_##SUFFIX##_p<1>(mode, block, params, s);                                        \
-      case 2: return stage_##SUFFIX##_p<2>(mode, block, params, s);                                        \
-      case 3: return stage_##SUFFIX##_p<3>(mode, block, params, s);                                        \
-      case 4: return stage_##SUFFIX##_p<4>(mode, block, params, s);                                        \
-    }                                                                                                      \
-    return cudaErrorInvalidValue;                                                                          \
-  }
+template <int P, class REAL, class PREAL, int FEAT>
+cudaError_t launch_stage_p(int mode, int block, const void* params, cudaStream_t s) {
+  if (mode == MODE_EVAL) return launch_stage_pm<P, REAL, PREAL, FEAT, MODE_EVAL>(block, params, s);
+  if (mode == MODE_STAGE) return launch_stage_pm<P, REAL, PREAL, FEAT, MODE_STAGE>(block, params, s);
+  return launch_stage_pm<P, REAL, PREAL, FEAT, MODE_RHS>(block, params, s);
+}
 
-// set-up and diagnostics launchers of one arithmetic
-#define DGSWE_DEFINE_AUX(SUFFIX, REAL, PREAL)                                                              \
-  cudaError_t static_##SUFFIX(int p, const Mesh& m, double gg, const double* hb64, void* hb, void* hbt,    \
-                              void* ghb, void* lin, cudaStream_t s) {                                      \
-    const unsigned g = (unsigned)((m.E + 127) / 128);                                                      \
-    REAL *a = (REAL*)hb, *b = (REAL*)hbt, *c = (REAL*)ghb, *d = (REAL*)lin;                                \
-    switch (p) {                                                                                           \
-      case 1: static_kernel<1, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
-      case 2: static_kernel<2, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
-      case 3: static_kernel<3, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
-      case 4: static_kernel<4, REAL><<<g, 128, 0, s>>>(m, gg, hb64, a, b, c, d); break;                    \
-      default: return cudaErrorInvalidValue;                                                               \
-    }                                                                                                      \
-    return cudaGetLastError();                                                                             \
-  }                                                                                                        \
-  cudaError_t diag_##SUFFIX(int p, const Mesh& m, const void* w, const void* hb, double det, double gg,    \
-                            double* partial, cudaStream_t s) {                                             \
-    const unsigned g = (unsigned)((m.E + 127) / 128);                                                      \
-    const REAL *a = (const REAL*)w, *b = (const REAL*)hb;                                                  \
-    switch (p) {                                                                                           \
-      case 1: diag_kernel<1, REAL, PREAL><<<g, 128, 0, s>>>(m, a, b, det, gg, partial); break;             \
-      case 2: diag_kernel<2, REAL, PREAL><<<g, 128, 0, s>>>(m, a, b, det, gg, partial); break;             \
-      case 3: diag_kernel<3, REAL, PREAL><<<g, 128, 0, s>>>(m, a, b, det, gg, partial); break;             \
-      case 4: diag_kernel<4, REAL, PREAL><<<g, 128, 0, s>>>(m, a, b, det, gg, partial); break;             \
-      default: return cudaErrorInvalidValue;                                                               \
-    }                                                                                                      \
-    return cudaGetLastError();                                                                             \
-  }
+// Set-up (bathymetry fields) and diagnostics launchers of one arithmetic
+// and order, compiled separately from dg_aux_inst.cu; the dispatchers
+// static_<suffix>(p, ...) and diag_<suffix>(p, ...) live in dg_dispatch.cu.
+#define DGSWE_STATIC_NAME(SUFFIX, P) DGSWE_PASTE4(static_, SUFFIX, _p, P)
+#define DGSWE_DIAG_NAME(SUFFIX, P) DGSWE_PASTE4(diag_, SUFFIX, _p, P)
+#define DGSWE_DECLARE_AUX_P(SUFFIX, P)                                                                   \
+  cudaError_t DGSWE_STATIC_NAME(SUFFIX, P)(const Mesh& m, double gg, const double* hb64, void* hb, void* hbt, \
+                                           void* ghb, void* lin, cudaStream_t s);                         \
+  cudaError_t DGSWE_DIAG_NAME(SUFFIX, P)(const Mesh& m, const void* w, const void* hb, double det, double gg, \
+                                         double* partial, cudaStream_t s);
+#define DGSWE_DECLARE_AUX_ALL(SUFFIX) \
+  DGSWE_DECLARE_AUX_P(SUFFIX, 1)      \
+  DGSWE_DECLARE_AUX_P(SUFFIX, 2)      \
+  DGSWE_DECLARE_AUX_P(SUFFIX, 3)      \
+  DGSWE_DECLARE_AUX_P(SUFFIX, 4)
+DGSWE_DECLARE_AUX_ALL(fp64)
+DGSWE_DECLARE_AUX_ALL(fp32p64)
+DGSWE_DECLARE_AUX_ALL(fp32p32)
+DGSWE_DECLARE_AUX_ALL(fp32pdf)
+
+template <int P, class REAL>
+cudaError_t launch_static_p(const Mesh& m, double gg, const double* hb64, void* hb, void* hbt, void* ghb, void* lin,
+                            cudaStream_t s) {
+  const unsigned g = (unsigned)((m.E + 127) / 128);
+  static_kernel<P, REAL><<<g, 128, 0, s>>>(m, gg, hb64, (REAL*)hb, (REAL*)hbt, (REAL*)ghb, (REAL*)lin);
+  return cudaGetLastError();
+}
+
+template <int P, class REAL, class PREAL>
+cudaError_t launch_diag_p(const Mesh& m, const void* w, const void* hb, double det, double gg, double* partial,
+                          cudaStream_t s) {
+  const unsigned g = (unsigned)((m.E + 127) / 128);
+  diag_kernel<P, REAL, PREAL><<<g, 128, 0, s>>>(m, (const REAL*)w, (const REAL*)hb, det, gg, partial);
+  return cudaGetLastError();
+}
+
+#define DGSWE_DECLARE_STAGE_ALL(SUFFIX) \
+  DGSWE_DECLARE_STAGE_P(SUFFIX, 1)      \
+  DGSWE_DECLARE_STAGE_P(SUFFIX, 2)      \
+  DGSWE_DECLARE_STAGE_P(SUFFIX, 3)      \
+  DGSWE_DECLARE_STAGE_P(SUFFIX, 4)
+DGSWE_DECLARE_STAGE_ALL(fp64)
+DGSWE_DECLARE_STAGE_ALL(fp32p64)
+DGSWE_DECLARE_STAGE_ALL(fp32p32)
+DGSWE_DECLARE_STAGE_ALL(fp32pdf)
+DGSWE_DECLARE_STAGE_ALL(fp64_gen)
+DGSWE_DECLARE_STAGE_ALL(fp32p64_gen)
+DGSWE_DECLARE_STAGE_ALL(fp32p32_gen)
 
 cudaError_t stage_fp64(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p64(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p32(int p, int mode, int block, const void* params, cudaStream_t s);
+cudaError_t stage_fp32pdf(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp64_gen(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p64_gen(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p32_gen(int p, int mode, int block, const void* params, cudaStream_t s);
@@ -90,6 +100,8 @@ cudaError_t static_fp64(int p, const Mesh& m, double g, const double* hb64, void
 cudaError_t static_fp32p64(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
                            void* lin, cudaStream_t s);
 cudaError_t static_fp32p32(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
+                           void* lin, cudaStream_t s);
+cudaError_t static_fp32pdf(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
                            void* lin, cudaStream_t s);
 
 // fill the derived geometry of a uniform mesh
@@ -114,6 +126,8 @@ cudaError_t diag_fp64(int p, const Mesh& m, const void* w, const void* hb, doubl
 cudaError_t diag_fp32p64(int p, const Mesh& m, const void* w, const void* hb, double det, double g,
                          double* partial, cudaStream_t s);
 cudaError_t diag_fp32p32(int p, const Mesh& m, const void* w, const void* hb, double det, double g,
+                         double* partial, cudaStream_t s);
+cudaError_t diag_fp32pdf(int p, const Mesh& m, const void* w, const void* hb, double det, double g,
                          double* partial, cudaStream_t s);
 
 }  // namespace dgswe

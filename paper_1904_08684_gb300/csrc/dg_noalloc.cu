@@ -93,6 +93,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   switch (arith) {
     case ARITH_FP64: e = static_fp64(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, lin, s); break;
     case ARITH_FP32_P64: e = static_fp32p64(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
+    case ARITH_FP32_PDF: e = static_fp32pdf(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
     default: e = static_fp32p32(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
   }
   if (e != cudaSuccess) return DG_ERR_CUDA;
@@ -118,6 +119,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
     switch (arith) {
       case ARITH_FP64: return stage_fp64(P, mode, block, &sp, s);
       case ARITH_FP32_P64: return stage_fp32p64(P, mode, block, &sp, s);
+      case ARITH_FP32_PDF: return stage_fp32pdf(P, mode, block, &sp, s);
       default: return stage_fp32p32(P, mode, block, &sp, s);
     }
   };
@@ -136,16 +138,19 @@ extern "C" dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, cons
   if (!cfg || !d_hb || !d_state_in || !d_rhs_out || d_state_in == d_rhs_out) return DG_ERR_ARG;
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->p < 1 || cfg->p > 4 || !(cfg->Lx > 0.0) || !(cfg->Ly > 0.0) ||
       !(cfg->g > 0.0) || cfg->vertex_xy || cfg->bc < 0 || cfg->bc > 1 || cfg->precision < 0 ||
-      cfg->precision > 1 || cfg->proj_precision < 0 || cfg->proj_precision > 1)
+      cfg->precision > 1 || cfg->proj_precision < 0 || cfg->proj_precision > 2)
     return DG_ERR_ARG;
   if (cfg->bc == DG_BC_PERIODIC && (cfg->nx < 2 || cfg->ny < 2)) return DG_ERR_ARG;
   if (cfg->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
+  if (cfg->precision == DG_PREC_FP32_MIXED && cfg->proj_precision == DG_PROJ_DF64 && cfg->p > 3)
+    return DG_ERR_UNSUPPORTED;
   if (cfg->block_size != 0 && (cfg->block_size < 32 || cfg->block_size > 128 || cfg->block_size % 32))
     return DG_ERR_ARG;
   if (2.0 * (double)cfg->nx * (double)cfg->ny > 1.0e8) return DG_ERR_ARG;
   const int arith = cfg->precision == DG_PREC_FP64
                         ? ARITH_FP64
-                        : (cfg->proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32 : ARITH_FP32_P64);
+                        : (cfg->proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32
+                                                 : cfg->proj_precision == DG_PROJ_DF64 ? ARITH_FP32_PDF : ARITH_FP32_P64);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (arith == ARITH_FP64) return run<double>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, s);
   return run<float>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, s);

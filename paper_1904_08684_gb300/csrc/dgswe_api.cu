@@ -47,6 +47,7 @@ struct dg_ctx {
   double* scal;          // [0],[1]: wave-speed slots, [2]: t, [3]: last dt
   unsigned* err;
   double* partial;       // diagnostics partial sums
+  double* stage;         // FP64 AoS staging buffer [3][E][K] for host copies
   void* rhs_vs;          // scratch of dg_rhs
   void* rhs_rec;
   int ep;                // eval buffer holding the current state's evaluation
@@ -77,7 +78,7 @@ dg_status validate(const dg_config* c) {
   if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
   if (c->rk_order < 1 || c->rk_order > 3) return DG_ERR_ARG;
   if (c->bc < 0 || c->bc > 2 || c->precision < 0 || c->precision > 1) return DG_ERR_ARG;
-  if (c->proj_precision < 0 || c->proj_precision > 1) return DG_ERR_ARG;
+  if (c->proj_precision < 0 || c->proj_precision > 2) return DG_ERR_ARG;
   if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
   if (!(c->tau_bf >= 0.0) || !std::isfinite(c->tau_bf) || !std::isfinite(c->f_c)) return DG_ERR_ARG;
   // the stage kernels are compiled for at most 128 threads per block
@@ -87,6 +88,9 @@ dg_status validate(const dg_config* c) {
   if (c->p == 0) return DG_ERR_UNSUPPORTED;
   if (c->bc == DG_BC_DIRICHLET && c->forcing != DG_FORCING_MANUFACTURED) return DG_ERR_UNSUPPORTED;
   if (c->vertex_xy && c->bc == DG_BC_PERIODIC) return DG_ERR_UNSUPPORTED;
+  if (c->precision == DG_PREC_FP32_MIXED && c->proj_precision == DG_PROJ_DF64 &&
+      (c->p > 3 || c->vertex_xy || c->forcing != DG_FORCING_NONE || c->bc == DG_BC_DIRICHLET))
+    return DG_ERR_UNSUPPORTED;
   if (2.0 * (double)c->nx * (double)c->ny > 4.0e9) return DG_ERR_ARG;
   return DG_OK;
 }
@@ -98,6 +102,7 @@ cudaError_t launch_stage_any(const dg_ctx* c, int mode, const void* params, cuda
   switch (c->arith) {
     case ARITH_FP64: return (gen ? stage_fp64_gen : stage_fp64)(c->P, mode, block, params, s);
     case ARITH_FP32_P64: return (gen ? stage_fp32p64_gen : stage_fp32p64)(c->P, mode, block, params, s);
+    case ARITH_FP32_PDF: return stage_fp32pdf(c->P, mode, block, params, s);
     default: return (gen ? stage_fp32p32_gen : stage_fp32p32)(c->P, mode, block, params, s);
   }
 }
@@ -263,6 +268,22 @@ __global__ void cvt_kernel_b(const float* __restrict__ a, double* __restrict__ b
   if (i < n) b[i] = double(a[i]);
 }
 
+// FP64 element-major [F][E][K] <-> context-precision SoA [F][K][E] on the device
+template <class Real>
+__global__ void aos_to_soa_kernel(const double* __restrict__ a, Real* __restrict__ b, long long E, int K, int F) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  for (int f = 0; f < F; ++f)
+    for (int i = 0; i < K; ++i) b[((long long)f * K + i) * E + e] = Real(a[((long long)f * E + e) * K + i]);
+}
+template <class Real>
+__global__ void soa_to_aos_kernel(const Real* __restrict__ b, double* __restrict__ a, long long E, int K, int F) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  for (int f = 0; f < F; ++f)
+    for (int i = 0; i < K; ++i) a[((long long)f * E + e) * K + i] = double(b[((long long)f * K + i) * E + e]);
+}
+
 // device FP64 -> context precision
 dg_status store_real(const dg_ctx* c, const double* src, void* dst, long long n, cudaStream_t s) {
   if (c->arith == ARITH_FP64) {
@@ -289,7 +310,8 @@ void free_ctx(dg_ctx* c) {
     for (auto& g : row)
       if (g.exec) cudaGraphExecDestroy(g.exec);
   void* bufs[] = {c->w[0], c->w[1], c->w[2], c->vs[0], c->vs[1], c->rec[0], c->rec[1], c->hb, c->hbt,
-                  c->ghb, c->lin, c->geo, c->vq, c->eq, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec};
+                  c->ghb, c->lin, c->geo, c->vq, c->eq, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec,
+                  c->stage};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -427,7 +449,8 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   c->NREC = 6 * c->P1 + 1;
   c->E = 2LL * cfg->nx * cfg->ny;
   c->arith = cfg->precision == DG_PREC_FP64 ? ARITH_FP64
-                                            : (cfg->proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32 : ARITH_FP32_P64);
+                                            : (cfg->proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32
+                                                 : cfg->proj_precision == DG_PROJ_DF64 ? ARITH_FP32_PDF : ARITH_FP32_P64);
   c->rsz = c->arith == ARITH_FP64 ? sizeof(double) : sizeof(float);
   c->stream = (cudaStream_t)stream;
   const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
@@ -506,6 +529,9 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
     case ARITH_FP64: le = static_fp64(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, c->lin, ss); break;
     case ARITH_FP32_P64:
       le = static_fp32p64(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss);
+      break;
+    case ARITH_FP32_PDF:
+      le = static_fp32pdf(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss);
       break;
     default: le = static_fp32p32(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss); break;
   }
@@ -647,43 +673,50 @@ dg_status dg_state_device(dg_ctx* c, void** d_state) {
   return DG_OK;
 }
 
+// Host copies of the state go through a device staging buffer (allocated on
+// first use, kept with the context): the caller's element-major arrays are
+// copied as they are (asynchronously; page-locked arrays copy fastest) and
+// transposed on the device.
+dg_status ensure_stage(dg_ctx* c) {
+  if (!c->stage) CK(cudaMalloc((void**)&c->stage, sizeof(double) * 3 * (size_t)c->K * c->E));
+  return DG_OK;
+}
+
 dg_status dg_get_state(dg_ctx* c, double* xi, double* qx, double* qy) {
   if (!c) return DG_ERR_ARG;
-  const long long E = c->E, KE = (long long)c->K * E;
-  double* tmp = nullptr;
-  CK(cudaMalloc(&tmp, sizeof(double) * 3 * KE));
-  dg_status s = load_real(c, c->w[0], tmp, 3 * KE, c->stream);
-  std::vector<double> h((size_t)3 * KE);
-  cudaError_t e = cudaMemcpyAsync(h.data(), tmp, sizeof(double) * 3 * KE, cudaMemcpyDeviceToHost, c->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  cudaFree(tmp);
+  dg_status s = ensure_stage(c);
   if (s != DG_OK) return s;
-  CK(e);
+  const long long E = c->E, KE = (long long)c->K * E;
+  const unsigned g = (unsigned)((E + 127) / 128);
+  if (c->arith == ARITH_FP64)
+    soa_to_aos_kernel<double><<<g, 128, 0, c->stream>>>((const double*)c->w[0], c->stage, E, c->K, 3);
+  else
+    soa_to_aos_kernel<float><<<g, 128, 0, c->stream>>>((const float*)c->w[0], c->stage, E, c->K, 3);
+  CK(cudaGetLastError());
   double* dst[3] = {xi, qx, qy};
-  for (int f = 0; f < 3; ++f) {
-    if (!dst[f]) continue;
-    const double* src = h.data() + (size_t)f * KE;
-    for (long long el = 0; el < E; ++el)
-      for (int i = 0; i < c->K; ++i) dst[f][(size_t)el * c->K + i] = src[(size_t)i * E + el];
-  }
+  for (int f = 0; f < 3; ++f)
+    if (dst[f])
+      CK(cudaMemcpyAsync(dst[f], c->stage + (size_t)f * KE, sizeof(double) * KE, cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   return DG_OK;
 }
 
 dg_status dg_set_state(dg_ctx* c, const double* xi, const double* qx, const double* qy, double t) {
   if (!c || !xi || !qx || !qy) return DG_ERR_ARG;
-  const long long E = c->E, KE = (long long)c->K * E;
-  double* tmp = nullptr;
-  CK(cudaMalloc(&tmp, sizeof(double) * 3 * KE));
-  const double* src[3] = {xi, qx, qy};
-  dg_status s = DG_OK;
-  for (int f = 0; f < 3 && s == DG_OK; ++f) s = upload_soa(src[f], E, c->K, tmp + (size_t)f * KE, c->stream);
-  if (s == DG_OK) s = store_real(c, tmp, c->w[0], 3 * KE, c->stream);
-  cudaError_t e = cudaMemcpyAsync(c->scal + 2, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream);
-  cudaError_t e2 = cudaStreamSynchronize(c->stream);
-  cudaFree(tmp);
+  dg_status s = ensure_stage(c);
   if (s != DG_OK) return s;
-  CK(e);
-  CK(e2);
+  const long long E = c->E, KE = (long long)c->K * E;
+  const double* src[3] = {xi, qx, qy};
+  for (int f = 0; f < 3; ++f)
+    CK(cudaMemcpyAsync(c->stage + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, c->stream));
+  const unsigned g = (unsigned)((E + 127) / 128);
+  if (c->arith == ARITH_FP64)
+    aos_to_soa_kernel<double><<<g, 128, 0, c->stream>>>(c->stage, (double*)c->w[0], E, c->K, 3);
+  else
+    aos_to_soa_kernel<float><<<g, 128, 0, c->stream>>>(c->stage, (float*)c->w[0], E, c->K, 3);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(c->scal + 2, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
   c->evaluated = false;
   return DG_OK;
 }
@@ -696,6 +729,9 @@ dg_status dg_diagnostics(dg_ctx* c, double* mass, double* energy) {
     case ARITH_FP64: e = diag_fp64(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream); break;
     case ARITH_FP32_P64:
       e = diag_fp32p64(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream);
+      break;
+    case ARITH_FP32_PDF:
+      e = diag_fp32pdf(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream);
       break;
     default: e = diag_fp32p32(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream); break;
   }

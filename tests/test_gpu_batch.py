@@ -16,12 +16,13 @@ SPECS = [(7, 5, 3, "periodic"), (12, 9, 1, "reflective"), (5, 6, 2, "periodic"),
          (9, 4, 1, "periodic"), (6, 6, 3, "reflective")]
 
 
-def _instance(k, nx, ny, p, bc, precision):
+def _instance(k, nx, ny, p, bc, precision, proj="fp64"):
     r = I.uniform(100 + k, 6)
     wl = I.Workload("b%d" % k, nx, ny, p, bc, 3, 0.2, 0, precision,
                     hb=I.fourier_bathymetry(12.0, [1.5 * r[0], 1.0 * r[1]], [1, 0], [1, 2], [0, 1]),
                     xi0=I.gaussian_sum([0.02 + 0.05 * r[2]], [0.1], [r[3]], [r[4]], periodic=(bc == "periodic")))
-    cfg = B.make_config(nx, ny, p, bc=bc, precision=precision, rk_order=3, cfl=0.2 + 0.1 * r[5])
+    cfg = B.make_config(nx, ny, p, bc=bc, precision=precision, rk_order=3, cfl=0.2 + 0.1 * r[5],
+                        proj_precision=proj)
     Q, E, K = B.dg_proj_num_nodes(p), wl.E, wl.K
     xy = torch.empty((2, Q, E), dtype=torch.float64, device="cuda")
     B.dg_proj_nodes(cfg, xy)
@@ -41,9 +42,10 @@ def _gpu():
     B.load()
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_batch_equals_single_contexts(precision):
-    inst = [_instance(k, *s, precision) for k, s in enumerate(SPECS)]
+@pytest.mark.parametrize("precision,proj", [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32"), ("fp32", "df64")])
+def test_batch_equals_single_contexts(precision, proj):
+    """the batched persistent kernel reproduces single contexts bit for bit"""
+    inst = [_instance(k, *s, precision, proj) for k, s in enumerate(SPECS)]
     steps = 15
     ref = []
     for cfg, f, E, K in inst:

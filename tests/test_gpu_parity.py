@@ -93,11 +93,14 @@ def test_rhs_matches_oracle_fp64(oracle_mod, p, bc):
 
 
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
-@pytest.mark.parametrize("proj", ["fp64", "fp32"])
+@pytest.mark.parametrize("proj", ["fp64", "fp32", "df64"])
 def test_rhs_fp32_state(oracle_mod, p, proj):
-    """FP32 state and contractions (velocity solve in FP64 or FP32): the RHS
-    agrees with the FP64 oracle to FP32 round-off amplified by the
-    Lax-Friedrichs jump term (|jump| ~ eps |w|, times lambda / h)."""
+    """FP32 state and contractions (velocity solve in FP64, FP32 or
+    double-float): the RHS agrees with the FP64 oracle to FP32 round-off
+    amplified by the Lax-Friedrichs jump term (|jump| ~ eps |w|, times
+    lambda / h).  The double-float solve is built for p <= 3."""
+    if proj == "df64" and p > 3:
+        pytest.skip("double-float solve is built for p <= 3")
     wl = I.waves_p2_512(n=13, p=p, ngauss=3)
     wl.ny = 11
     o = oracle_mod.Oracle(wl.nx, wl.ny, p, bc="periodic")
@@ -179,14 +182,16 @@ def test_fixed_dt_rk1_step(oracle_mod):
 
 # ------------------------------------------------------------------ FP32 state
 @pytest.mark.slow
-def test_fp32_mixed_hump_p3_1000_steps(oracle_mod):
-    """FP32 state and contractions, FP64 velocity solve, p = 3, 1000 SSP-RK3
-    steps against the FP64 oracle: relative L2 per field <= 1e-5."""
+@pytest.mark.parametrize("proj", ["fp64", "df64"])
+def test_fp32_mixed_hump_p3_1000_steps(oracle_mod, proj):
+    """FP32 state and contractions, FP64 (or double-float) velocity solve,
+    p = 3, 1000 SSP-RK3 steps against the FP64 oracle: relative L2 per field
+    <= 1e-5."""
     wl = I.hump_p3_32()
     o = oracle_mod.Oracle(wl.nx, wl.ny, 3, bc="reflective", rk_order=3, cfl=0.2)
     hb, xi, U, V = _state(o, wl, with_flow=False)
     xr, Ur, Vr, tr, _ = o.run(hb, xi, U, V, wl.steps)
-    ctx = B.dg_init(_cfg(wl, precision="fp32"), hb, xi, U, V)
+    ctx = B.dg_init(_cfg(wl, precision="fp32", proj_precision=proj), hb, xi, U, V)
     try:
         m0, _ = B.dg_diagnostics(ctx)
         t = B.dg_run(ctx, wl.steps)
