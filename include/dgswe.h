@@ -225,11 +225,13 @@ dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out);
 dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy);
 
 /* Autotuner: times trial_steps steps with 32, 64, 96 and 128 elements per
- * work item (one thread per element), restores the state, keeps the fastest;
- * *block_out gets it and ms_out (NULL or 4 doubles) the ms per step of each. */
+ * work item (one thread per element), restoring the state after each, and
+ * keeps the fastest; *block_out (may be NULL) receives it and ms_out (NULL or
+ * 4 doubles) the ms per step of each.  State and times are unchanged on
+ * return.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out);
 
-/* set the elements per work item (32, 64, 96 or 128) */
+/* set the elements per work item (32, 64, 96 or 128; DG_ERR_ARG otherwise) */
 dg_status dg_batch_set_block(dg_batch* b, int block);
 
 /* degrees of freedom updated per RK stage: sum over instances of 3 K E */

@@ -515,47 +515,72 @@ double or_eval_point(void* hv, const double* coef, int e, double x, double y) {
 
 /* quadrature nodes for projecting point data: E x Q x 2 physical coords */
 int or_num_proj_nodes(void* hv) { return ((or_ctx*)hv)->proj.n; }
-void or_proj_nodes(void* hv, double* xy) {
-  or_ctx* h = hv;
+static void proj_nodes_elem(const or_ctx* h, int e, double* xy) {
   const int Q = h->proj.n;
-  for (int e = 0; e < h->E; ++e) {
-    const double* B = h->B + 4 * e;
-    for (int q = 0; q < Q; ++q) {
-      double xr = h->proj.x[q], yr = h->proj.y[q];
-      xy[(e * Q + q) * 2] = h->ax[3 * e] + B[0] * xr + B[1] * yr;
-      xy[(e * Q + q) * 2 + 1] = h->ay[3 * e] + B[2] * xr + B[3] * yr;
-    }
+  const double* B = h->B + 4 * e;
+  for (int q = 0; q < Q; ++q) {
+    double xr = h->proj.x[q], yr = h->proj.y[q];
+    xy[q * 2] = h->ax[3 * e] + B[0] * xr + B[1] * yr;
+    xy[q * 2 + 1] = h->ay[3 * e] + B[2] * xr + B[3] * yr;
   }
 }
+void or_proj_nodes(void* hv, double* xy) {
+  or_ctx* h = hv;
+  for (int e = 0; e < h->E; ++e) proj_nodes_elem(h, e, xy + (size_t)e * h->proj.n * 2);
+}
+/* the same for the n listed elements only: n x Q x 2 */
+void or_proj_nodes_sub(void* hv, const int* elems, int n, double* xy) {
+  or_ctx* h = hv;
+  for (int i = 0; i < n; ++i) proj_nodes_elem(h, elems[i], xy + (size_t)i * h->proj.n * 2);
+}
 
-/* L2 projection of point data (E x Q values at or_proj_nodes) onto P^p:
- * solve M c = (f, phi) elementwise with quadrature mass matrix. */
+/* L2 projection of point data (Q values at the element's or_proj_nodes) onto
+ * the first nf basis functions: solve M c = (f, phi) with the quadrature mass
+ * matrix of element e. */
+static int project_elem(const or_ctx* h, int nf, int e, const double* vals, double* coef) {
+  const int K = nf, Q = h->proj.n;
+  double M[OR_MAXK * OR_MAXK], b[OR_MAXK];
+  memset(M, 0, sizeof M);
+  memset(b, 0, sizeof b);
+  for (int q = 0; q < Q; ++q) {
+    double phi[OR_MAXK];
+    for (int i = 0; i < K; ++i) phi[i] = poly_eval(&h->basis[i], h->proj.x[q], h->proj.y[q]);
+    double w = h->proj.w[q] * fabs(h->det[e]);
+    for (int a = 0; a < K; ++a) {
+      b[a] += w * vals[q] * phi[a];
+      for (int c = 0; c < K; ++c) M[a * K + c] += w * phi[a] * phi[c];
+    }
+  }
+  if (!chol_solve(K, M, b, 1)) return 0;
+  for (int a = 0; a < K; ++a) coef[a] = b[a];
+  return 1;
+}
+
+/* every element: vals E x Q, coef E x nf */
 int or_project_n(void* hv, int nf, const double* vals, double* coef) {
   or_ctx* h = hv;
-  const int K = nf, Q = h->proj.n;
   if (nf < 1 || nf > OR_MAXK) return OR_ERR_ARG;
+  const size_t Q = (size_t)h->proj.n;
   int ok = 1;
 #pragma omp parallel for schedule(static) reduction(&& : ok) num_threads(nthreads(h))
-  for (int e = 0; e < h->E; ++e) {
-    double M[OR_MAXK * OR_MAXK], b[OR_MAXK];
-    memset(M, 0, sizeof M);
-    memset(b, 0, sizeof b);
-    for (int q = 0; q < Q; ++q) {
-      double phi[OR_MAXK];
-      for (int i = 0; i < K; ++i) phi[i] = poly_eval(&h->basis[i], h->proj.x[q], h->proj.y[q]);
-      double w = h->proj.w[q] * fabs(h->det[e]);
-      for (int a = 0; a < K; ++a) {
-        b[a] += w * vals[e * Q + q] * phi[a];
-        for (int c = 0; c < K; ++c) M[a * K + c] += w * phi[a] * phi[c];
-      }
-    }
-    if (!chol_solve(K, M, b, 1)) ok = 0;
-    for (int a = 0; a < K; ++a) coef[e * K + a] = b[a];
-  }
+  for (int e = 0; e < h->E; ++e)
+    if (!project_elem(h, nf, e, vals + (size_t)e * Q, coef + (size_t)e * nf)) ok = 0;
   return ok ? OR_OK : OR_ERR_ARG;
 }
 int or_project(void* hv, const double* vals, double* coef) { return or_project_n(hv, ((or_ctx*)hv)->K, vals, coef); }
 int or_project_hb(void* hv, const double* vals, double* coef) { return or_project_n(hv, ((or_ctx*)hv)->Kb, vals, coef); }
+
+/* the n listed elements: vals n x Q; rows elems[i] of coef (E x nf) */
+int or_project_sub(void* hv, int nf, const int* elems, int n, const double* vals, double* coef) {
+  or_ctx* h = hv;
+  if (nf < 1 || nf > OR_MAXK) return OR_ERR_ARG;
+  const size_t Q = (size_t)h->proj.n;
+  int ok = 1;
+#pragma omp parallel for schedule(static) reduction(&& : ok) num_threads(nthreads(h))
+  for (int i = 0; i < n; ++i)
+    if (!project_elem(h, nf, elems[i], vals + (size_t)i * Q, coef + (size_t)elems[i] * nf)) ok = 0;
+  return ok ? OR_OK : OR_ERR_ARG;
+}
 
 /* u-projection of Eq. (12) on one element: (u H, psi) = (q, psi). */
 static int project_u_elem(const or_ctx* h, int e, const double* hb, const double* xi, const double* U,

@@ -70,7 +70,9 @@ def _load():
         lib.or_eval_point.restype = ctypes.c_double
         lib.or_num_proj_nodes.argtypes = [vp]
         lib.or_proj_nodes.argtypes = [vp, dp]
+        lib.or_proj_nodes_sub.argtypes = [vp, ip, ctypes.c_int, dp]
         lib.or_project.argtypes = [vp, dp, dp]
+        lib.or_project_sub.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int, dp, dp]
         lib.or_project_u.argtypes = [vp, dp, dp, dp, dp, dp, dp]
         lib.or_rhs.argtypes = [vp, dp, dp, dp, dp, ctypes.c_double, ip, ctypes.c_int, dp, dp, dp]
         lib.or_max_wave_speed.argtypes = [vp, dp, dp, dp, dp]
@@ -159,11 +161,29 @@ class Oracle:
         return self.lib.or_eval_point(self._h, _ptr(coef), int(e), float(x), float(y))
 
     # ---- projection ---------------------------------------------------------
-    def proj_nodes(self):
+    def proj_nodes(self, elems=None):
+        """physical projection nodes, shape (E, Q, 2), or (len(elems), Q, 2)"""
         Q = self.lib.or_num_proj_nodes(self._h)
-        xy = np.zeros((self.E, Q, 2))
-        self.lib.or_proj_nodes(self._h, _ptr(xy))
+        if elems is None:
+            xy = np.zeros((self.E, Q, 2))
+            self.lib.or_proj_nodes(self._h, _ptr(xy))
+            return xy
+        el = np.ascontiguousarray(elems, dtype=np.int32)
+        xy = np.zeros((len(el), Q, 2))
+        self.lib.or_proj_nodes_sub(self._h, el.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(el), _ptr(xy))
         return xy
+
+    def project_sub(self, vals, elems, out, hb=False):
+        """L2 projection of values at proj_nodes(elems) (shape (len(elems), Q))
+        into rows ``elems`` of ``out`` (shape (E, K), or (E, Kb) with hb)"""
+        el = np.ascontiguousarray(elems, dtype=np.int32)
+        vals = _f64(vals)
+        nf = self.Kb if hb else self.K
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.shape == (self.E, nf)
+        if self.lib.or_project_sub(self._h, nf, el.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), len(el),
+                                   _ptr(vals), _ptr(out)):
+            raise RuntimeError("oracle projection failed")
+        return out
 
     def project(self, f):
         """L2 projection of the function f(x, y) (numpy-vectorised) onto P^p."""

@@ -66,10 +66,7 @@ def _nvcc():
 
 
 def _sources():
-    out = [os.path.join(CSRC, u) for u in SOURCES]
-    out += [os.path.join(CSRC, f) for f in ("dg_kernels.cuh", "dg_launch.cuh", "dg_batch.cuh", "gen_tables.py")]
-    out.append(os.path.join(INCLUDE, "dgswe.h"))
-    return out
+    return [os.path.join(CSRC, u) for u in SOURCES] + _headers()
 
 
 def _stale():
@@ -79,10 +76,19 @@ def _stale():
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
-def _compile(job):
+def _headers():
+    return [os.path.join(CSRC, f) for f in ("dg_kernels.cuh", "dg_launch.cuh", "dg_batch.cuh", "gen_tables.py")] + \
+        [os.path.join(INCLUDE, "dgswe.h")]
+
+
+def _compile(job, force=False):
     unit, objname, defs = job
     src = os.path.join(CSRC, unit)
     obj = os.path.join(BUILD, objname)
+    if not force and os.path.exists(obj):
+        t = os.path.getmtime(obj)
+        if all(os.path.getmtime(d) <= t for d in [src] + _headers()):
+            return obj
     cmd = [_nvcc()] + NVCC_FLAGS + defs + ["-I" + BUILD, "-I" + INCLUDE, "-I" + CSRC, "-c", src, "-o", obj]
     t0 = time.time()
     res = subprocess.run(cmd, capture_output=True, text=True)
@@ -105,7 +111,7 @@ def build_library(force=False, verbose=False):
     jobs = sorted(_units(), key=_cost, reverse=True)
     workers = max(1, min(len(jobs), os.cpu_count() or 1))
     with cf.ThreadPoolExecutor(max_workers=workers) as ex:
-        objs = list(ex.map(_compile, jobs))
+        objs = list(ex.map(lambda j: _compile(j, force), jobs))
     tmp = LIB + ".tmp%d" % os.getpid()
     subprocess.check_call([_nvcc()] + ARCH + ["-shared", "-o", tmp] + objs)
     os.replace(tmp, LIB)

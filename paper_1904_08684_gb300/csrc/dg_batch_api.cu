@@ -153,7 +153,11 @@ dg_status get_graph(dg_batch* b, cudaGraphExec_t* out) {
   return DG_OK;
 }
 
-// work items of blockDim elements, most expensive order first
+// Work items of `block` elements, the most expensive order first (all p = 3
+// items, then p = 2, then p = 1).  All warps of an SM then run the same
+// order's code at the same time; queues that mix orders (each class spread
+// evenly, so that FP64-bound and FP32-bound items overlap) measured 1.2-5x
+// slower, the warps stalling on instruction fetch.
 dg_status build_items(dg_batch* b, int block) {
   std::vector<BatchItem> items;
   for (int p = 3; p >= 1; --p)
@@ -439,63 +443,66 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
 }
 
 // Autotuner: times trial_steps steps at every candidate block size (elements
-// per work item) on the batch's own state, restores the state, keeps the
-// fastest.  ms_out[4] receives the time per step of 32, 64, 96, 128.
+// per work item) on the batch's own state, restoring the state after each,
+// and keeps the fastest.  ms_out[4] receives the time per step of 32, 64, 96
+// and 128.
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out) {
   if (!b || trial_steps < 1) return DG_ERR_ARG;
-  dg_status s;
   CK(cudaStreamSynchronize(b->stream));
   // snapshot of everything a step changes
   void* save = nullptr;
   double* save_t = nullptr;
-  CK(cudaMalloc(&save, b->sz_state));
-  CK(cudaMalloc((void**)&save_t, sizeof(double) * 3 * b->n));
-  CK(cudaMemcpyAsync(save, b->w[0], b->sz_state, cudaMemcpyDeviceToDevice, b->stream));
-  CK(cudaMemcpyAsync(save_t, b->t, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, b->stream));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
   const int ep0 = b->ep, lc0 = b->lc;
-  const bool ev0 = b->evaluated;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
   const int cand[4] = {32, 64, 96, 128};
   double best = 1e300;
   int best_block = b->block;
-  for (int c = 0; c < 4; ++c) {
-    if ((s = build_items(b, cand[c])) != DG_OK) return s;
+  dg_status s = DG_OK;
+  cudaError_t ce = cudaMalloc(&save, b->sz_state);
+  if (ce == cudaSuccess) ce = cudaMalloc((void**)&save_t, sizeof(double) * b->n);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(save, b->w[0], b->sz_state, cudaMemcpyDeviceToDevice, b->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(save_t, b->t, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, b->stream);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  for (int c = 0; c < 4 && ce == cudaSuccess && s == DG_OK; ++c) {
+    const int block = cand[c];
+    if ((s = build_items(b, block)) != DG_OK) break;
     b->evaluated = false;
     b->ep = ep0;
     b->lc = lc0;
-    if ((s = dg_batch_run(b, 1, nullptr)) != DG_OK) return s;   // warm-up, graph build
-    CK(cudaEventRecord(e0, b->stream));
-    for (int k = 0; k < trial_steps; ++k) {
+    if ((s = dg_batch_run(b, 1, nullptr)) != DG_OK) break;   // warm-up, graph build
+    ce = cudaEventRecord(e0, b->stream);
+    for (int k = 0; k < trial_steps && ce == cudaSuccess && s == DG_OK; ++k) {
       cudaGraphExec_t g;
-      if ((s = get_graph(b, &g)) != DG_OK) return s;
-      CK(cudaGraphLaunch(g, b->stream));
+      if ((s = get_graph(b, &g)) != DG_OK) break;
+      ce = cudaGraphLaunch(g, b->stream);
       b->ep = (b->ep + b->S) & 1;
       if (b->adaptive) b->lc = 1 - b->lc;
     }
-    CK(cudaEventRecord(e1, b->stream));
-    CK(cudaEventSynchronize(e1));
+    if (ce == cudaSuccess && s == DG_OK) ce = cudaEventRecord(e1, b->stream);
+    if (ce == cudaSuccess && s == DG_OK) ce = cudaEventSynchronize(e1);
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ce == cudaSuccess && s == DG_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
     const double per = ms / trial_steps;
     if (ms_out) ms_out[c] = per;
-    if (per < best) {
+    if (ce == cudaSuccess && s == DG_OK && per < best) {
       best = per;
-      best_block = cand[c];
+      best_block = block;
     }
-    CK(cudaMemcpyAsync(b->w[0], save, b->sz_state, cudaMemcpyDeviceToDevice, b->stream));
-    CK(cudaMemcpyAsync(b->t, save_t, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, b->stream));
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->w[0], save, b->sz_state, cudaMemcpyDeviceToDevice, b->stream);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(b->t, save_t, sizeof(double) * b->n, cudaMemcpyDeviceToDevice, b->stream);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  CK(cudaStreamSynchronize(b->stream));
-  cudaFree(save);
-  cudaFree(save_t);
+  const cudaError_t ce2 = cudaStreamSynchronize(b->stream);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (save) cudaFree(save);
+  if (save_t) cudaFree(save_t);
   b->ep = ep0;
   b->lc = lc0;
   b->evaluated = false;   // re-evaluate the restored state
-  (void)ev0;
+  if (s != DG_OK) return s;
+  if (ce != cudaSuccess) return cuda_status(ce);
+  if (ce2 != cudaSuccess) return cuda_status(ce2);
   if ((s = build_items(b, best_block)) != DG_OK) return s;
   if (block_out) *block_out = best_block;
   return DG_OK;

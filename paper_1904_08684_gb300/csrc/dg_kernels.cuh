@@ -443,6 +443,53 @@ __device__ __forceinline__ float mad(float a, float b, float c) { return fmaf(a,
 __device__ __forceinline__ df64 mad(df64 a, df64 b, df64 c) { return a * b + c; }
 
 // ---------------------------------------------------------------------------
+// Sums of products in the arithmetic of the velocity solve.  For double and
+// float: a fused multiply-add chain.  For df64: a compensated dot product
+// (Ogita, Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci.
+// Comput. 26 (2005), algorithm Dot2, extended to double-float operands):
+// each product is split exactly into its rounded value and its error with a
+// fused multiply-add, the running sum stays in one float whose rounding
+// errors are gathered by two-sum into a second float, and the two are joined
+// once at the end.  The result is as accurate as a double-float evaluation,
+// but a term costs 11-12 FP32 operations instead of ~27, and the dependent
+// chain through the terms is one addition long.
+template <class PR>
+struct SolveAcc {
+  PR s;
+  __device__ __forceinline__ explicit SolveAcc(PR x) : s(x) {}
+  __device__ __forceinline__ void add(PR a, PR b) { s = mad(a, b, s); }   // s += a b
+  template <class H>
+  __device__ __forceinline__ void add_c(double t, H h) { s = mad(PR(t), PR(h), s); }   // s += t h, t constant
+  __device__ __forceinline__ PR get() const { return s; }
+};
+
+template <>
+struct SolveAcc<df64> {
+  float s, c;   // running sum and the sum of its rounding errors
+  __device__ __forceinline__ explicit SolveAcc(df64 x) : s(x.hi), c(x.lo) {}
+  // add p + e, where p + e is an exact product and |e| <= ulp(p)
+  __device__ __forceinline__ void add_exact(float p, float e) {
+    const float t = __fadd_rn(s, p);
+    const float z = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  }
+  __device__ __forceinline__ void add(df64 a, df64 b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    const float e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, __fmaf_rn(a.hi, b.hi, -p)));
+    add_exact(p, e);
+  }
+  // s += t h with t a compile-time constant and h a float
+  __device__ __forceinline__ void add_c(double t, float h) {
+    const df64 tt(t);   // split at compile time once inlined
+    const float p = __fmul_rn(tt.hi, h);
+    add_exact(p, __fmaf_rn(tt.lo, h, __fmaf_rn(tt.hi, h, -p)));
+  }
+  __device__ __forceinline__ df64 get() const { return df_two_sum(s, c); }
+};
+
+// ---------------------------------------------------------------------------
 // Velocity projection (Eq. (12)): A u = U, A v = V with
 // A_ab = sum_n T[n][a][b] H_n (SPD iff H > 0 on the element), solved by an
 // LDL^T factorisation in precision PR.  Returns false if a pivot is not
@@ -451,50 +498,54 @@ template <int P, class PR, class R>
 __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R* V, R* u, R* v) {
   using Tb = RefTables<P>;
   constexpr int K = Tb::K;
-  PR Hd[K], L[K][K], Dg[K], rD[K], y[K];
-  sfor<0, K>([&](auto n) { Hd[CV(n)] = PR(H[CV(n)]); });
+  // the depth enters the double-float solve as the exact float it is
+  using HT = typename std::conditional<std::is_same<PR, df64>::value, R, PR>::type;
+  HT Hd[K];
+  PR L[K][K], Dg[K], rD[K], y[K];
+  sfor<0, K>([&](auto n) { Hd[CV(n)] = HT(H[CV(n)]); });
   bool ok = true;
   // left-looking LDL^T: column j uses W_k = L_jk D_k (k < j)
   sfor<0, K>([&](auto jj) {
     constexpr int j = CV(jj);
     PR W[K > 1 ? K : 1];
-    PR d = PR(0);
+    SolveAcc<PR> d(PR(0));
     sfor<0, K>([&](auto n) {
       constexpr double t = Tb::T[CV(n)][j][j];
-      if constexpr (t != 0.0) d = mad(PR(t), Hd[CV(n)], d);
+      if constexpr (t != 0.0) d.add_c(t, Hd[CV(n)]);
     });
     sfor<0, j>([&](auto k) {
       W[CV(k)] = L[j][CV(k)] * Dg[CV(k)];
-      d = mad(-L[j][CV(k)], W[CV(k)], d);
+      d.add(-L[j][CV(k)], W[CV(k)]);
     });
-    ok = ok && (d > PR(0));
-    Dg[j] = d;
-    rD[j] = PR(1) / d;
+    const PR dj = d.get();
+    ok = ok && (dj > PR(0));
+    Dg[j] = dj;
+    rD[j] = PR(1) / dj;
     sfor<j + 1, K>([&](auto ii) {
       constexpr int i = CV(ii);
-      PR a = PR(0);
+      SolveAcc<PR> a(PR(0));
       sfor<0, K>([&](auto n) {
         constexpr double t = Tb::T[CV(n)][i][j];
-        if constexpr (t != 0.0) a = mad(PR(t), Hd[CV(n)], a);
+        if constexpr (t != 0.0) a.add_c(t, Hd[CV(n)]);
       });
-      sfor<0, j>([&](auto k) { a = mad(-L[i][CV(k)], W[CV(k)], a); });
-      L[i][j] = a * rD[j];
+      sfor<0, j>([&](auto k) { a.add(-L[i][CV(k)], W[CV(k)]); });
+      L[i][j] = a.get() * rD[j];
     });
   });
   // two right-hand sides: L y = b, y <- y / D, L^T x = y
   auto solve = [&](const R* b, R* x) {
     sfor<0, K>([&](auto ii) {
       constexpr int i = CV(ii);
-      PR s = PR(b[i]);
-      sfor<0, i>([&](auto k) { s = mad(-L[i][CV(k)], y[CV(k)], s); });
-      y[i] = s;
+      SolveAcc<PR> s{PR(b[i])};
+      sfor<0, i>([&](auto k) { s.add(-L[i][CV(k)], y[CV(k)]); });
+      y[i] = s.get();
     });
     sfor<0, K>([&](auto rr) {
       constexpr int i = K - 1 - CV(rr);
-      PR s = y[i] * rD[i];
-      sfor<i + 1, K>([&](auto k) { s = mad(-L[CV(k)][i], y[CV(k)], s); });
-      y[i] = s;
-      x[i] = R(s);
+      SolveAcc<PR> s(y[i] * rD[i]);
+      sfor<i + 1, K>([&](auto k) { s.add(-L[CV(k)][i], y[CV(k)]); });
+      y[i] = s.get();
+      x[i] = R(y[i]);
     });
   };
   solve(U, u);
