@@ -218,7 +218,7 @@ def _dtype(precision, proj):
     """arithmetic of the path: state/contractions, plus the velocity solve"""
     if precision == "fp64":
         return "f64"
-    return {"fp64": "f32+f64solve", "fp32": "f32", "df64": "f32+df64solve"}[proj]
+    return {"fp64": "f32+f64solve", "fp32": "f32", "df64": "f32+df64solve", "mixed": "f32+f64refinedsolve"}[proj]
 
 
 def _cfg_of(B, wl, args):
@@ -480,7 +480,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="waves-p2-512", choices=sorted(WORKLOADS))
-    ap.add_argument("--proj", default="fp64", choices=["fp64", "fp32", "df64"],
+    ap.add_argument("--proj", default="fp64", choices=["fp64", "fp32", "df64", "mixed"],
                     help="velocity-solve arithmetic of the FP32 state path")
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--e2e-steps", type=int, default=5)

@@ -66,10 +66,14 @@ typedef enum {
 
 typedef enum { DG_BC_PERIODIC = 0, DG_BC_REFLECTIVE = 1, DG_BC_DIRICHLET = 2 } dg_bc;
 typedef enum { DG_PREC_FP64 = 0, DG_PREC_FP32_MIXED = 1 } dg_precision;
-/* Arithmetic of the velocity solve of DG_PREC_FP32_MIXED: FP64 (default), FP32,
- * or double-float (pairs of FP32 numbers, ~48 significant bits, on the FP32
- * units; p <= 3, uniform meshes without forcing only). */
-typedef enum { DG_PROJ_FP64 = 0, DG_PROJ_FP32 = 1, DG_PROJ_DF64 = 2 } dg_proj_precision;
+/* Arithmetic of the velocity solve of DG_PREC_FP32_MIXED: FP64 (default);
+ * FP32; double-float (pairs of FP32 numbers, ~48 significant bits, on the
+ * FP32 units; p <= 3); or MIXED: FP32 LDL^T and solves plus one step of
+ * iterative refinement with the residual formed in FP64, which returns the
+ * FP64 solution to within FP32 rounding while the FP32 factors hold
+ * (elements whose FP32 pivots fail or spread by more than 2^10 take the FP64
+ * solve).  DF64 and MIXED: uniform meshes without forcing only. */
+typedef enum { DG_PROJ_FP64 = 0, DG_PROJ_FP32 = 1, DG_PROJ_DF64 = 2, DG_PROJ_MIXED = 3 } dg_proj_precision;
 /* §3.1 convergence test of the paper: xi = 2.3 - 0.4 S, U = 0.6 + 0.04 S,
  * V = 0.3 + 0.04 S, S = sin(pi (x + y + 0.2 t) / 600), on the bathymetry
  * h_b = 1 + x/1000 + 2 y/1000 (which the caller projects), with the body force
@@ -115,20 +119,27 @@ typedef struct dg_ctx dg_ctx;
 /* Number of basis functions K = (p+1)(p+2)/2 (0 for p outside 0..4). */
 int dg_num_basis(int p);
 
+/* Number of bathymetry coefficients Kb per element: h_b is a DG field of
+ * P^max(p,1) (at p = 0 a piecewise-constant h_b would drop the source
+ * g xi grad h_b of Eq. (5)), so Kb = K for p >= 1 and 3 for p = 0. */
+int dg_num_basis_bathymetry(int p);
+
 /* Number of triangles 2 nx ny of a configuration (0 if invalid). */
 long long dg_num_elements(const dg_config* cfg);
 
 /* Create a context (paper §2.2 discrete unknowns c_ei, Eqs. (13)-(14)).
- * hb: bathymetry coefficients, host FP64 AoS [E][K] (h_b is a DG field of the
- * same order; the caller L2-projects it, see dg_project).  xi, qx, qy: the
+ * hb: bathymetry coefficients, host FP64 AoS [E][Kb], Kb =
+ * dg_num_basis_bathymetry(p) (h_b is a DG field of order max(p, 1); the
+ * caller L2-projects it, see dg_project with that order).  xi, qx, qy: the
  * initial state, host FP64 AoS [E][K].  stream: a cudaStream_t or NULL.
  * Allocates every device buffer the time loop needs; *out receives the
  * context.  Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_init(const dg_config* cfg, const double* hb, const double* xi, const double* qx,
                   const double* qy, void* stream, dg_ctx** out);
 
-/* As dg_init, but hb, xi, qx, qy are DEVICE arrays, FP64 SoA [K][E] (one
- * field each), e.g. the output of dg_project.  They are copied. */
+/* As dg_init, but hb, xi, qx, qy are DEVICE arrays, FP64 SoA [Kb][E] (h_b)
+ * and [K][E] (one field each), e.g. the output of dg_project.  They are
+ * copied. */
 dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_xi, const void* d_qx,
                          const void* d_qy, void* stream, dg_ctx** out);
 
@@ -180,7 +191,8 @@ dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, voi
  *   cfg:        mesh, order, boundary, precision as for dg_init (p = 1..4,
  *               uniform mesh, periodic or reflective walls, no forcing);
  *               dt, cfl, rk_order are ignored.
- *   d_hb:       device FP64 SoA [K][E] bathymetry coefficients (input).
+ *   d_hb:       device FP64 SoA [Kb][E] bathymetry coefficients (input),
+ *               Kb = dg_num_basis_bathymetry(p).
  *   d_state_in: device SoA [3][K][E] state in cfg's precision (input).
  *   d_rhs_out:  device SoA [3][K][E] (output), must not overlap d_state_in.
  *   stream:     cudaStream_t or NULL; the call is asynchronous on it.
@@ -213,7 +225,7 @@ typedef struct dg_batch dg_batch;
  * instances share precision, proj_precision, rk_order and fixed-vs-CFL time
  * stepping (else DG_ERR_ARG).  d_hb[i], d_xi[i], d_qx[i], d_qy[i]: DEVICE
  * FP64 SoA [K_i][E_i] arrays (copied).  Errors: DG_ERR_ARG,
- * DG_ERR_UNSUPPORTED (p = 4, Dirichlet), DG_ERR_OOM, DG_ERR_CUDA. */
+ * DG_ERR_UNSUPPORTED (p = 0 or 4, Dirichlet), DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
                         const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out);
 

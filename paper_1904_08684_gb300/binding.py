@@ -16,14 +16,14 @@ from . import build as _build
 DG_OK, DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA, DG_ERR_DRY, DG_ERR_NONFINITE, DG_ERR_TIMEOUT = range(8)
 DG_BC_PERIODIC, DG_BC_REFLECTIVE, DG_BC_DIRICHLET = 0, 1, 2
 DG_PREC_FP64, DG_PREC_FP32_MIXED = 0, 1
-DG_PROJ_FP64, DG_PROJ_FP32, DG_PROJ_DF64 = 0, 1, 2
-PROJ = {"fp64": DG_PROJ_FP64, "fp32": DG_PROJ_FP32, "df64": DG_PROJ_DF64}
+DG_PROJ_FP64, DG_PROJ_FP32, DG_PROJ_DF64, DG_PROJ_MIXED = 0, 1, 2, 3
+PROJ = {"fp64": DG_PROJ_FP64, "fp32": DG_PROJ_FP32, "df64": DG_PROJ_DF64, "mixed": DG_PROJ_MIXED}
 
 BC = {"periodic": DG_BC_PERIODIC, "reflective": DG_BC_REFLECTIVE, "dirichlet": DG_BC_DIRICHLET}
 PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
 
 # every entry point declared in include/dgswe.h
-EXPORTS = ["dg_num_basis", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
+EXPORTS = ["dg_num_basis", "dg_num_basis_bathymetry", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
            "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc",
            "dg_batch_init", "dg_batch_run", "dg_batch_get_state", "dg_batch_autotune", "dg_batch_set_block",
@@ -87,6 +87,7 @@ def load(build_if_missing=True):
     vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
     cp = ctypes.POINTER(dg_config)
     lib.dg_num_basis.argtypes = [ctypes.c_int]
+    lib.dg_num_basis_bathymetry.argtypes = [ctypes.c_int]
     lib.dg_num_elements.argtypes = [cp]
     lib.dg_num_elements.restype = ctypes.c_longlong
     lib.dg_init.argtypes = [cp, dp, dp, dp, dp, vp, ctypes.POINTER(vp)]
@@ -165,15 +166,20 @@ def dg_num_basis(p):
     return load().dg_num_basis(int(p))
 
 
+def dg_num_basis_bathymetry(p):
+    return load().dg_num_basis_bathymetry(int(p))
+
+
 def dg_num_elements(cfg):
     return load().dg_num_elements(ctypes.byref(cfg))
 
 
 def dg_init(cfg, hb, xi, qx, qy, stream=None):
-    """Context from host FP64 (E, K) arrays; returns an opaque handle."""
+    """Context from host FP64 arrays, hb (E, Kb) and the state (E, K);
+    returns an opaque handle."""
     lib = load()
-    E, K = dg_num_elements(cfg), dg_num_basis(cfg.p)
-    arrs = [_host(a, E, K) for a in (hb, xi, qx, qy)]
+    E, K, Kb = dg_num_elements(cfg), dg_num_basis(cfg.p), dg_num_basis_bathymetry(cfg.p)
+    arrs = [_host(hb, E, Kb)] + [_host(a, E, K) for a in (xi, qx, qy)]
     h = ctypes.c_void_p()
     _check(lib.dg_init(ctypes.byref(cfg), *[_hptr(a) for a in arrs], _stream(stream), ctypes.byref(h)),
            "dg_init")

@@ -24,7 +24,8 @@ LIB = os.path.join(BUILD, "libdgswe.so")
 # compilations run in parallel rather than a few long ones.
 #   suffix: (state type, velocity-solve type, highest order)
 ARITHS = {"fp64": ("double", "double", 4), "fp32p64": ("float", "double", 4),
-          "fp32p32": ("float", "float", 4), "fp32pdf": ("float", "df64", 3)}
+          "fp32p32": ("float", "float", 4), "fp32pdf": ("float", "df64", 3),
+          "fp32pir": ("float", "MixedIR", 4)}
 PLAIN_UNITS = ["dgswe_api.cu", "dg_project.cu", "dg_noalloc.cu", "dg_batch_api.cu", "dg_dispatch.cu"]
 
 
@@ -33,14 +34,14 @@ def _units():
     out = [(u, u.replace(".cu", ".o"), []) for u in PLAIN_UNITS]
     for sfx, (real, preal, pmax) in ARITHS.items():
         base = ["-DDG_SUFFIX=" + sfx, "-DDG_REAL=" + real, "-DDG_PREAL=" + preal]
-        for p in range(1, pmax + 1):
+        for p in range(0, pmax + 1):
             out.append(("dg_aux_inst.cu", "aux_%s_p%d.o" % (sfx, p), base + ["-DDG_P=%d" % p]))
         for mode in (0, 1):
             out.append(("dg_batch_inst.cu", "batch_%s_m%d.o" % (sfx, mode), base + ["-DDG_MODE=%d" % mode]))
         # the general-mesh feature set is not built for the double-float solve
-        for feat in ((0, 1) if sfx != "fp32pdf" else (0,)):
+        for feat in ((0, 1) if sfx not in ("fp32pdf", "fp32pir") else (0,)):
             name = sfx + ("_gen" if feat else "")
-            for p in range(1, pmax + 1):
+            for p in range(0, pmax + 1):
                 out.append(("dg_stage_inst.cu", "stage_%s_p%d.o" % (name, p),
                             ["-DDG_SUFFIX=" + name, "-DDG_REAL=" + real, "-DDG_PREAL=" + preal,
                              "-DDG_FEAT=%d" % feat, "-DDG_P=%d" % p]))

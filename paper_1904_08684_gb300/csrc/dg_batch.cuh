@@ -143,5 +143,6 @@ DGSWE_BATCH_DECLARE(fp64)
 DGSWE_BATCH_DECLARE(fp32p64)
 DGSWE_BATCH_DECLARE(fp32p32)
 DGSWE_BATCH_DECLARE(fp32pdf)
+DGSWE_BATCH_DECLARE(fp32pir)
 
 }  // namespace dgswe

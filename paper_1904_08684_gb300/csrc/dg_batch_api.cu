@@ -80,6 +80,7 @@ cudaError_t launch_batch(const dg_batch* b, int mode, const BatchArgs& a, cudaSt
     case ARITH_FP64: return batch_launch_fp64(mode, b->grid, b->block, a, s);
     case ARITH_FP32_P64: return batch_launch_fp32p64(mode, b->grid, b->block, a, s);
     case ARITH_FP32_PDF: return batch_launch_fp32pdf(mode, b->grid, b->block, a, s);
+    case ARITH_FP32_PIR: return batch_launch_fp32pir(mode, b->grid, b->block, a, s);
     default: return batch_launch_fp32p32(mode, b->grid, b->block, a, s);
   }
 }
@@ -176,6 +177,7 @@ dg_status build_items(dg_batch* b, int block) {
     case ARITH_FP64: e = batch_occupancy_fp64(block, &occ); break;
     case ARITH_FP32_P64: e = batch_occupancy_fp32p64(block, &occ); break;
     case ARITH_FP32_PDF: e = batch_occupancy_fp32pdf(block, &occ); break;
+    case ARITH_FP32_PIR: e = batch_occupancy_fp32pir(block, &occ); break;
     default: e = batch_occupancy_fp32p32(block, &occ); break;
   }
   CK(e);
@@ -220,9 +222,11 @@ dg_status store_real(const dg_batch* b, const double* src, void* dst, long long 
 }
 
 dg_status validate_one(const dg_config* c) {
-  if (c->nx < 2 || c->ny < 2 || c->p < 1 || c->p > 3) return c->p > 3 ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
+  if (c->nx < 2 || c->ny < 2 || c->p < 0 || c->p > 4) return DG_ERR_ARG;
+  if (c->p == 0 || c->p == 4) return DG_ERR_UNSUPPORTED;   // the batched kernel holds p = 1..3
   if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
   if (c->rk_order < 1 || c->rk_order > 3 || c->bc < 0 || c->bc > 2) return DG_ERR_ARG;
+  if (c->precision < 0 || c->precision > 1 || c->proj_precision < 0 || c->proj_precision > 3) return DG_ERR_ARG;
   if (c->bc == DG_BC_DIRICHLET || c->vertex_xy || c->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
   if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
   if (2.0 * c->nx * (double)c->ny > 2.0e9) return DG_ERR_ARG;
@@ -247,10 +251,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   dg_batch* b = new (std::nothrow) dg_batch();
   if (!b) return DG_ERR_OOM;
   b->n = n;
-  b->arith = cfgs[0].precision == DG_PREC_FP64
-                 ? ARITH_FP64
-                 : (cfgs[0].proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32
-                    : cfgs[0].proj_precision == DG_PROJ_DF64 ? ARITH_FP32_PDF : ARITH_FP32_P64);
+  b->arith = arith_of(cfgs[0].precision, cfgs[0].proj_precision);
   b->rsz = b->arith == ARITH_FP64 ? 8 : 4;
   b->S = cfgs[0].rk_order;
   b->adaptive = !(cfgs[0].dt > 0.0);
@@ -353,6 +354,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
       case ARITH_FP64: e = static_fp64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, pl, s); break;
       case ARITH_FP32_P64: e = static_fp32p64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
       case ARITH_FP32_PDF: e = static_fp32pdf(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
+      case ARITH_FP32_PIR: e = static_fp32pir(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
       default: e = static_fp32p32(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
     }
   }

@@ -2,7 +2,7 @@
 // stage_<suffix>(p, ...) calls stage_<suffix>_p<p> (dg_stage_inst.cu),
 // static_/diag_<suffix>(p, ...) call *_p<p> (dg_aux_inst.cu) and
 // batch_launch_<suffix>(mode, ...) calls batch_launch_<suffix>_m<mode>
-// (dg_batch_inst.cu).  Orders outside 1..4 return cudaErrorInvalidValue.
+// (dg_batch_inst.cu).  Orders outside 0..4 return cudaErrorInvalidValue.
 #include "dg_batch.cuh"
 #include "dg_launch.cuh"
 
@@ -11,6 +11,7 @@ namespace dgswe {
 #define DGSWE_DISPATCH(SUFFIX)                                                                  \
   cudaError_t stage_##SUFFIX(int p, int mode, int block, const void* params, cudaStream_t s) {         \
     switch (p) {                                                                                      \
+      case 0: return stage_##SUFFIX##_p0(mode, block, params, s);                                      \
       case 1: return stage_##SUFFIX##_p1(mode, block, params, s);                                      \
       case 2: return stage_##SUFFIX##_p2(mode, block, params, s);                                      \
       case 3: return stage_##SUFFIX##_p3(mode, block, params, s);                                      \
@@ -26,6 +27,7 @@ DGSWE_DISPATCH(fp64_gen)
 DGSWE_DISPATCH(fp32p64_gen)
 DGSWE_DISPATCH(fp32p32_gen)
 DGSWE_DISPATCH(fp32pdf)
+DGSWE_DISPATCH(fp32pir)
 
 // the double-float velocity solve is built for p <= 3: its p = 4 entries
 // reject the call
@@ -54,6 +56,7 @@ cudaError_t diag_fp32pdf_p4(const Mesh&, const void*, const void*, double, doubl
   cudaError_t static_##SUFFIX(int p, const Mesh& m, double gg, const double* hb64, void* hb, void* hbt,         \
                               void* ghb, void* lin, cudaStream_t s) {                                           \
     switch (p) {                                                                                                \
+      case 0: return static_##SUFFIX##_p0(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
       case 1: return static_##SUFFIX##_p1(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
       case 2: return static_##SUFFIX##_p2(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
       case 3: return static_##SUFFIX##_p3(m, gg, hb64, hb, hbt, ghb, lin, s);                                   \
@@ -64,6 +67,7 @@ cudaError_t diag_fp32pdf_p4(const Mesh&, const void*, const void*, double, doubl
   cudaError_t diag_##SUFFIX(int p, const Mesh& m, const void* w, const void* hb, double det, double gg,         \
                             double* partial, cudaStream_t s) {                                                  \
     switch (p) {                                                                                                \
+      case 0: return diag_##SUFFIX##_p0(m, w, hb, det, gg, partial, s);                                         \
       case 1: return diag_##SUFFIX##_p1(m, w, hb, det, gg, partial, s);                                         \
       case 2: return diag_##SUFFIX##_p2(m, w, hb, det, gg, partial, s);                                         \
       case 3: return diag_##SUFFIX##_p3(m, w, hb, det, gg, partial, s);                                         \
@@ -77,11 +81,13 @@ DGSWE_AUX_DISPATCH(fp64)
 DGSWE_AUX_DISPATCH(fp32p64)
 DGSWE_AUX_DISPATCH(fp32p32)
 DGSWE_AUX_DISPATCH(fp32pdf)
+DGSWE_AUX_DISPATCH(fp32pir)
 
 // batched persistent kernel: mode 0 = evaluation, 1 = stage
 DGSWE_BATCH_DISPATCH(fp64)
 DGSWE_BATCH_DISPATCH(fp32p64)
 DGSWE_BATCH_DISPATCH(fp32p32)
 DGSWE_BATCH_DISPATCH(fp32pdf)
+DGSWE_BATCH_DISPATCH(fp32pir)
 
 }  // namespace dgswe

@@ -43,6 +43,13 @@ struct Dims {
   static constexpr int P1 = P + 1;                 // Legendre modes on an edge
   static constexpr int K1 = P * (P + 1) / 2;       // basis of P^{p-1}
   static constexpr int NREC = 6 * P1 + 1;          // side record length
+  // the bathymetry lives in P^max(p,1) (at p = 0 a piecewise-constant h_b
+  // would lose the source g xi grad h_b): its order, basis size, edge modes
+  // and the basis size of its gradient's space
+  static constexpr int PB = P > 0 ? P : 1;
+  static constexpr int KB = (PB + 1) * (PB + 2) / 2;
+  static constexpr int PB1 = PB + 1;
+  static constexpr int KB1 = PB * (PB + 1) / 2;
 };
 
 // error word bits
@@ -491,20 +498,18 @@ struct SolveAcc<df64> {
 
 // ---------------------------------------------------------------------------
 // Velocity projection (Eq. (12)): A u = U, A v = V with
-// A_ab = sum_n T[n][a][b] H_n (SPD iff H > 0 on the element), solved by an
-// LDL^T factorisation in precision PR.  Returns false if a pivot is not
-// positive (dry element).
-template <int P, class PR, class R>
-__device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R* V, R* u, R* v) {
+// A_ab = sum_n T[n][a][b] H_n (SPD iff H > 0 on the element).
+
+// LDL^T factorisation of A in precision PR (left-looking: column j uses
+// W_k = L_jk D_k, k < j).  Hd: the depth coefficients (HT = PR, or float for
+// the double-float solve, whose depth enters as the exact float it is).
+// Returns false if a pivot is not positive (dry element).
+template <int P, class PR, class HT>
+__device__ __forceinline__ bool ldlt_factor(const HT* Hd, PR (&L)[RefTables<P>::K][RefTables<P>::K],
+                                            PR* Dg, PR* rD) {
   using Tb = RefTables<P>;
   constexpr int K = Tb::K;
-  // the depth enters the double-float solve as the exact float it is
-  using HT = typename std::conditional<std::is_same<PR, df64>::value, R, PR>::type;
-  HT Hd[K];
-  PR L[K][K], Dg[K], rD[K], y[K];
-  sfor<0, K>([&](auto n) { Hd[CV(n)] = HT(H[CV(n)]); });
   bool ok = true;
-  // left-looking LDL^T: column j uses W_k = L_jk D_k (k < j)
   sfor<0, K>([&](auto jj) {
     constexpr int j = CV(jj);
     PR W[K > 1 ? K : 1];
@@ -532,25 +537,123 @@ __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R
       L[i][j] = a.get() * rD[j];
     });
   });
-  // two right-hand sides: L y = b, y <- y / D, L^T x = y
-  auto solve = [&](const R* b, R* x) {
-    sfor<0, K>([&](auto ii) {
-      constexpr int i = CV(ii);
-      SolveAcc<PR> s{PR(b[i])};
-      sfor<0, i>([&](auto k) { s.add(-L[i][CV(k)], y[CV(k)]); });
-      y[i] = s.get();
-    });
-    sfor<0, K>([&](auto rr) {
-      constexpr int i = K - 1 - CV(rr);
-      SolveAcc<PR> s(y[i] * rD[i]);
-      sfor<i + 1, K>([&](auto k) { s.add(-L[CV(k)][i], y[CV(k)]); });
-      y[i] = s.get();
-      x[i] = R(y[i]);
-    });
-  };
-  solve(U, u);
-  solve(V, v);
   return ok;
+}
+
+// L y = b, y <- y / D, L^T x = y
+template <int P, class PR, class B, class X>
+__device__ __forceinline__ void ldlt_solve(const PR (&L)[RefTables<P>::K][RefTables<P>::K], const PR* rD,
+                                           const B* b, X* x) {
+  constexpr int K = RefTables<P>::K;
+  PR y[K];
+  sfor<0, K>([&](auto ii) {
+    constexpr int i = CV(ii);
+    SolveAcc<PR> s{PR(b[i])};
+    sfor<0, i>([&](auto k) { s.add(-L[i][CV(k)], y[CV(k)]); });
+    y[i] = s.get();
+  });
+  sfor<0, K>([&](auto rr) {
+    constexpr int i = K - 1 - CV(rr);
+    SolveAcc<PR> s(y[i] * rD[i]);
+    sfor<i + 1, K>([&](auto k) { s.add(-L[CV(k)][i], y[CV(k)]); });
+    y[i] = s.get();
+    x[i] = X(y[i]);
+  });
+}
+
+// Marker type of the mixed-precision solve (FP32 state only): LDL^T and both
+// triangular solves in FP32, then one step of iterative refinement with the
+// residual r = b - A x0 formed in FP64 (A assembled entry by entry in FP64
+// and used at once), x = x0 + A^{-1} r with the FP32 factors (Wilkinson's
+// mixed-precision refinement).  With kappa(A) * K * 2^-24 << 1 the result is
+// the FP64 solution to within FP32 rounding; elements whose FP32 pivots
+// spread over more than 2^10 (kappa estimate), or fail, take the FP64 solve.
+struct MixedIR {};
+
+template <int P, class PR, class R>
+__device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R* V, R* u, R* v);
+
+template <int P, class R>
+__device__ __forceinline__ bool project_velocity_ir(const R* H, const R* U, const R* V, R* u, R* v) {
+  using Tb = RefTables<P>;
+  constexpr int K = Tb::K;
+  float L[K][K], Dg[K], rD[K];
+  float Hf[K];
+  sfor<0, K>([&](auto n) { Hf[CV(n)] = float(H[CV(n)]); });
+  bool ok = ldlt_factor<P, float>(Hf, L, Dg, rD);
+  float dmin = Dg[0], dmax = Dg[0];
+  sfor<1, K>([&](auto j) {
+    dmin = fminf(dmin, Dg[CV(j)]);
+    dmax = fmaxf(dmax, Dg[CV(j)]);
+  });
+  if (!ok || !(dmax <= 1024.f * dmin)) return project_velocity<P, double>(H, U, V, u, v);
+  float u0[K], v0[K];
+  ldlt_solve<P>(L, rD, U, u0);
+  ldlt_solve<P>(L, rD, V, v0);
+  // residuals in FP64: A_ab = sum_n T[n][a][b] H_n, entry by entry
+  double Hd[K], ru[K], rv[K], ud[K], vd[K];
+  sfor<0, K>([&](auto n) {
+    Hd[CV(n)] = double(H[CV(n)]);
+    ru[CV(n)] = double(U[CV(n)]);
+    rv[CV(n)] = double(V[CV(n)]);
+    ud[CV(n)] = double(u0[CV(n)]);
+    vd[CV(n)] = double(v0[CV(n)]);
+  });
+  sfor<0, K>([&](auto aa) {
+    constexpr int a = CV(aa);
+    sfor<0, a + 1>([&](auto bb) {
+      constexpr int b = CV(bb);
+      double A = 0.0;
+      bool any = false;
+      sfor<0, K>([&](auto n) {
+        constexpr double t = Tb::T[CV(n)][a][b];
+        if constexpr (t != 0.0) {
+          A = fma(t, Hd[CV(n)], A);
+          any = true;
+        }
+      });
+      if (any) {
+        ru[a] = fma(-A, ud[b], ru[a]);
+        rv[a] = fma(-A, vd[b], rv[a]);
+        if constexpr (a != b) {
+          ru[b] = fma(-A, ud[a], ru[b]);
+          rv[b] = fma(-A, vd[a], rv[b]);
+        }
+      }
+    });
+  });
+  float rf[K], du[K], dv[K];
+  sfor<0, K>([&](auto i) { rf[CV(i)] = float(ru[CV(i)]); });
+  ldlt_solve<P>(L, rD, rf, du);
+  sfor<0, K>([&](auto i) { rf[CV(i)] = float(rv[CV(i)]); });
+  ldlt_solve<P>(L, rD, rf, dv);
+  // explicit rounding: the last solve step leaves u0 = y rD, and a
+  // contracted y rD + du would depend on the compilation context
+  sfor<0, K>([&](auto i) {
+    u[CV(i)] = R(__fadd_rn(u0[CV(i)], du[CV(i)]));
+    v[CV(i)] = R(__fadd_rn(v0[CV(i)], dv[CV(i)]));
+  });
+  return true;
+}
+
+// Solve in precision PR (double, float, df64), or MixedIR (see above).
+template <int P, class PR, class R>
+__device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R* V, R* u, R* v) {
+  if constexpr (std::is_same<PR, MixedIR>::value) {
+    return project_velocity_ir<P>(H, U, V, u, v);
+  } else {
+    using Tb = RefTables<P>;
+    constexpr int K = Tb::K;
+    // the depth enters the double-float solve as the exact float it is
+    using HT = typename std::conditional<std::is_same<PR, df64>::value, R, PR>::type;
+    HT Hd[K];
+    PR L[K][K], Dg[K], rD[K];
+    sfor<0, K>([&](auto n) { Hd[CV(n)] = HT(H[CV(n)]); });
+    const bool ok = ldlt_factor<P, PR>(Hd, L, Dg, rD);
+    ldlt_solve<P>(L, rD, U, u);
+    ldlt_solve<P>(L, rD, V, v);
+    return ok;
+  }
 }
 
 // phi^_i(x^, y^), i < K, from the exact monomial tables
@@ -651,7 +754,7 @@ __device__ __forceinline__ void dirichlet_flux(const StageParams<Real>& sp, long
                                                const Real* tx, const Real* tU, const Real* tV, const Real* tu,
                                                const Real* tv, const Real* th, const Real* un, const Real* Hs,
                                                Real* rb, double t_eval, unsigned& err) {
-  constexpr int P1 = P + 1;
+  constexpr int P1 = P + 1, PB1 = Dims<P>::PB1;   // h_b traces: PB1 modes
   const long long E = sp.m.E;
   const double g = double(sp.g), nxd = double(nx), nyd = double(ny);
   double ax, ay, B11, B12, B21, B22;
@@ -662,25 +765,26 @@ __device__ __forceinline__ void dirichlet_flux(const StageParams<Real>& sp, long
     x = ax + B11 * xr + B12 * yr;
     y = ay + B21 * xr + B22 * yr;
   };
-  auto evalL = [&](const Real* tau, const double* L) {
+  auto evalN = [&](const Real* tau, const double* L, int n) {
     double v = 0.0;
-    for (int j = 0; j < P1; ++j) v = fma(double(tau[j]), L[j], v);
+    for (int j = 0; j < n; ++j) v = fma(double(tau[j]), L[j], v);
     return v;
   };
+  auto evalL = [&](const Real* tau, const double* L) { return evalN(tau, L, P1); };
   // wave speed: both sides at s = 0, 1/2, 1
   double lam = 0.0;
   for (int k = 0; k < 3; ++k) {
     const double s = 0.5 * k;
-    double L[P1], pp = 1.0, pc = 2.0 * s - 1.0;   // orthonormal shifted Legendre at s
+    double L[PB1], pp = 1.0, pc = 2.0 * s - 1.0;   // orthonormal shifted Legendre at s
     L[0] = 1.0;
-    if (P1 > 1) L[1] = sqrt(3.0) * pc;
-    for (int j = 1; j + 1 < P1; ++j) {
+    L[1] = sqrt(3.0) * pc;
+    for (int j = 1; j + 1 < PB1; ++j) {
       const double pn = ((2 * j + 1) * (2.0 * s - 1.0) * pc - j * pp) / (j + 1);
       pp = pc;
       pc = pn;
       L[j + 1] = sqrt(2.0 * (j + 1) + 1.0) * pn;
     }
-    const double Hin = evalL(Hs, L), unin = evalL(un, L), hbin = evalL(th, L);
+    const double Hin = evalN(Hs, L, PB1), unin = evalL(un, L), hbin = evalN(th, L, PB1);
     double x, y, xg, Ug, Vg;
     point(s, x, y);
     ms_state(x, y, t_eval, xg, Ug, Vg);
@@ -697,7 +801,7 @@ __device__ __forceinline__ void dirichlet_flux(const StageParams<Real>& sp, long
     const double s = row[0], w = row[1];
     const double* L = row + 2;
     const double xi_m = evalL(tx, L), U_m = evalL(tU, L), V_m = evalL(tV, L);
-    const double u_m = evalL(tu, L), v_m = evalL(tv, L), hb = evalL(th, L);
+    const double u_m = evalL(tu, L), v_m = evalL(tv, L), hb = evalN(th, L, PB1);
     double x, y, xi_p, U_p, V_p;
     point(s, x, y);
     ms_state(x, y, t_eval, xi_p, U_p, V_p);
@@ -730,21 +834,28 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
                                             const Real* U, const Real* V, const Real* u, const Real* v,
                                             unsigned& err, double t_eval) {
   using D = Dims<P>;
-  constexpr int P1 = D::P1, NREC = D::NREC;
+  constexpr int P1 = D::P1, NREC = D::NREC, PB1 = D::PB1;
   const long long E = sp.m.E;
   Real nx, ny, len;
   edge_geom<FEAT>(sp.m, e, t, NN, nx, ny, len);
   const Real hl = Real(0.5) * len;
   const Real hg = Real(0.5) * sp.g;
-  Real tx[P1], tU[P1], tV[P1], th[P1], xe[P1], Hs[P1];
+  // h_b traces have PB1 >= P1 modes (one more at p = 0): all of them enter
+  // the depth at the wave-speed points; the projection of xi (xi + 2 h_b)
+  // onto P^p needs only the first P1 (at p = 0, the mean of h_b on the edge)
+  Real tx[P1], tU[P1], tV[P1], th[PB1], xe[P1], Hs[PB1];
   trace<NN, P>(xi, tx);
   trace<NN, P>(U, tU);
   trace<NN, P>(V, tV);
-  sfor<0, P1>([&](auto j) {
+  sfor<0, PB1>([&](auto j) {
     constexpr int jj = CV(j);
-    th[jj] = sp.hbt[(NN * P1 + jj) * E + e];
-    xe[jj] = fma(Real(2), th[jj], tx[jj]);
-    Hs[jj] = tx[jj] + th[jj];
+    th[jj] = sp.hbt[(NN * PB1 + jj) * E + e];
+    if constexpr (jj < P1) {
+      xe[jj] = fma(Real(2), th[jj], tx[jj]);
+      Hs[jj] = tx[jj] + th[jj];
+    } else {
+      Hs[jj] = th[jj];
+    }
   });
   Real Pp[P1], PU[P1], PV[P1], un[P1];
   lprod<P>(tx, xe, Pp);
@@ -798,7 +909,7 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
     rb[(5 * P1 + jj) * E] = tV[jj];
   });
   // wave speed of this side at s = 0, 1/2, 1 (|u.n| is sign-free)
-  const Real h0 = edge_point<P, 0>(Hs), h1 = edge_point<P, 1>(Hs), h2 = edge_point<P, 2>(Hs);
+  const Real h0 = edge_point<D::PB, 0>(Hs), h1 = edge_point<D::PB, 1>(Hs), h2 = edge_point<D::PB, 2>(Hs);
   const Real u0 = edge_point<P, 0>(un), u1 = edge_point<P, 1>(un), u2 = edge_point<P, 2>(un);
   if (!(h0 > Real(0)) || !(h1 > Real(0)) || !(h2 > Real(0))) err |= ERRF_DRY;
   const Real l0 = fabs(u0) + sqrt(sp.g * h0);
@@ -826,7 +937,8 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
   // volume integrals (A~, grad phi_a) (Eqs. (15)-(16)): grad phi_a lies in
   // P^{p-1}, so only the first K1 coefficients of each projected product count
   constexpr bool kLin = std::is_same<Real, double>::value;
-  Real Puu[K1], Puv[K1], Pvu[K1], Pvv[K1], Pxx[K1];
+  constexpr int K1A = K1 > 0 ? K1 : 1;   // array extent (p = 0 has no volume term)
+  Real Puu[K1A], Puv[K1A], Pvu[K1A], Pvv[K1A], Pxx[K1A];
   momentum_products<P>(U, V, u, v, Puu, Puv, Pvu, Pvv);
   // pressure 1/2 g xi (xi + 2 h_b): in FP64 the part g xi h_b, linear in xi,
   // and the source g xi grad h_b of Eq. (5) come from the static matrices
@@ -839,16 +951,17 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
     sfor<0, K>([&](auto i) { xe[CV(i)] = fma(Real(2), hb[CV(i)], xi[CV(i)]); });
     tprod<P, K1, K>(xi, xe, Pxx);
     // g sum_{i,m} T[a][i][m] xi_i ghb_m, ghb = det B * coefficients of grad h_b
-    Real gx[K1], gy[K1];
-    sfor<0, K1>([&](auto m) {
+    constexpr int KB1 = D::KB1;   // grad h_b lies in P^{max(p,1)-1}
+    Real gx[KB1], gy[KB1];
+    sfor<0, KB1>([&](auto m) {
       gx[CV(m)] = sp.ghb[CV(m) * E + e];
-      gy[CV(m)] = sp.ghb[(K1 + CV(m)) * E + e];
+      gy[CV(m)] = sp.ghb[(KB1 + CV(m)) * E + e];
     });
-    tprod<P, K, K1>(xi, gx, Sx);
-    tprod<P, K, K1>(xi, gy, Sy);
+    tprod<P, K, KB1>(xi, gx, Sx);
+    tprod<P, K, KB1>(xi, gy, Sy);
   }
   const Real hg = Real(0.5) * sp.g;
-  Real FxU[K1], FyV[K1];
+  Real FxU[K1A], FyV[K1A];
   sfor<0, K1>([&](auto i) {
     FxU[CV(i)] = fma(hg, Pxx[CV(i)], Puu[CV(i)]);
     FyV[CV(i)] = fma(hg, Pxx[CV(i)], Pvv[CV(i)]);
@@ -1088,53 +1201,57 @@ __global__ void __launch_bounds__(128, (stage_min_blocks<P, Real>())) stage_kern
   if (blockIdx.x == 0 && threadIdx.x == 0 && sp.lam_clear) *sp.lam_clear = 0.0;
 }
 
-// Static per-element fields of the bathymetry: edge traces and the
-// det-scaled gradient coefficients  ghb_r = G_rr * (d^_r h_b) (uniform mesh).
+// Static per-element fields of the bathymetry h_b in P^PB, PB = max(p, 1):
+// its coefficients, its edge traces (PB + 1 Legendre modes) and the
+// det-scaled gradient coefficients gh_r = sum_c G_rc (d^_c h_b) in P^{PB-1}.
+// The reference tables of order PB serve the order-p indices too (the basis
+// is hierarchical).
 template <int P, class Real>
 __global__ void static_kernel(Mesh m, double g, const double* __restrict__ hb64, Real* hb, Real* hbt, Real* ghb,
                               Real* lin) {
   using D = Dims<P>;
-  using Tb = RefTables<P>;
-  constexpr int K = D::K, P1 = D::P1, K1 = D::K1;
+  constexpr int PB = D::PB;
+  using Tb = RefTables<PB>;
+  constexpr int K = D::K, K1 = D::K1, KB = D::KB, PB1 = D::PB1, KB1 = D::KB1;
   const long long E = m.E;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   const int t = (int)(e & 1);
-  double h[K];
-  sfor<0, K>([&](auto i) {
+  double h[KB];
+  sfor<0, KB>([&](auto i) {
     h[CV(i)] = hb64[CV(i) * E + e];
     hb[CV(i) * E + e] = Real(h[CV(i)]);
   });
   auto tr = [&](auto nn) {
-    double tau[P1];
-    trace<CV(nn), P>(h, tau);
-    sfor<0, P1>([&](auto j) { hbt[(CV(nn) * P1 + CV(j)) * E + e] = Real(tau[CV(j)]); });
+    double tau[PB1];
+    trace<CV(nn), PB>(h, tau);
+    sfor<0, PB1>([&](auto j) { hbt[(CV(nn) * PB1 + CV(j)) * E + e] = Real(tau[CV(j)]); });
   };
   sfor<0, 3>(tr);
   double G[2][2];
   elem_G<1>(m, e, t, G[0][0], G[0][1], G[1][0], G[1][1]);
   // reference derivative coefficients d_c,m = sum_i S[c][i][m] h_i and the
   // det-scaled physical gradient gh_r = sum_c G_rc d_c
-  double d[2][K1 > 0 ? K1 : 1];
+  double d[2][KB1];
   sfor<0, 2>([&](auto c) {
-    sfor<0, K1>([&](auto mm) {
+    sfor<0, KB1>([&](auto mm) {
       double acc = 0.0;
-      sfor<0, K>([&](auto i) {
+      sfor<0, KB>([&](auto i) {
         constexpr double s = Tb::S[CV(c)][CV(i)][CV(mm)];
         if constexpr (s != 0.0) acc = fma(s, h[CV(i)], acc);
       });
       d[CV(c)][CV(mm)] = acc;
     });
   });
-  double gh[2][K1 > 0 ? K1 : 1];
+  double gh[2][KB1];
   sfor<0, 2>([&](auto r) {
-    sfor<0, K1>([&](auto mm) {
+    sfor<0, KB1>([&](auto mm) {
       gh[CV(r)][CV(mm)] = G[CV(r)][0] * d[0][CV(mm)] + G[CV(r)][1] * d[1][CV(mm)];
-      ghb[(CV(r) * K1 + CV(mm)) * E + e] = Real(gh[CV(r)][CV(mm)]);
+      ghb[(CV(r) * KB1 + CV(mm)) * E + e] = Real(gh[CV(r)][CV(mm)]);
     });
   });
   if (!lin) return;
-  // lin[r][a][k]: coefficient of xi_k in the r-momentum volume + source
+  // lin[r][a][k] (a, k < K): coefficient of xi_k in the r-momentum volume + source
   //   g sum_c G_rc sum_{i<K1} S[c][a][i] sum_m T[i][k][m] h_m  (pressure g xi h_b)
   // + g sum_m T[a][k][m] gh_r,m                              (source g xi d_r h_b)
   sfor<0, K>([&](auto a) {
@@ -1145,7 +1262,7 @@ __global__ void static_kernel(Mesh m, double g, const double* __restrict__ hb64,
           constexpr double s = Tb::S[CV(c)][CV(a)][CV(i)];
           if constexpr (s != 0.0) {
             double th = 0.0;
-            sfor<0, K>([&](auto mm) {
+            sfor<0, KB>([&](auto mm) {
               constexpr double tt = Tb::T[CV(i)][CV(k)][CV(mm)];
               if constexpr (tt != 0.0) th = fma(tt, h[CV(mm)], th);
             });
@@ -1155,7 +1272,7 @@ __global__ void static_kernel(Mesh m, double g, const double* __restrict__ hb64,
       });
       sfor<0, 2>([&](auto r) {
         double src = 0.0;
-        sfor<0, K1>([&](auto mm) {
+        sfor<0, KB1>([&](auto mm) {
           constexpr double tt = Tb::T[CV(a)][CV(k)][CV(mm)];
           if constexpr (tt != 0.0) src = fma(tt, gh[CV(r)][CV(mm)], src);
         });

@@ -11,7 +11,18 @@
 namespace dgswe {
 
 // arithmetic of one context: state/contractions and velocity solve
-enum Arith { ARITH_FP64 = 0, ARITH_FP32_P64 = 1, ARITH_FP32_P32 = 2, ARITH_FP32_PDF = 3 };
+enum Arith { ARITH_FP64 = 0, ARITH_FP32_P64 = 1, ARITH_FP32_P32 = 2, ARITH_FP32_PDF = 3, ARITH_FP32_PIR = 4 };
+
+// arithmetic of a configuration (precision and velocity-solve precision)
+inline int arith_of(int precision, int proj_precision) {
+  if (precision == 0) return ARITH_FP64;
+  switch (proj_precision) {
+    case 1: return ARITH_FP32_P32;
+    case 2: return ARITH_FP32_PDF;
+    case 3: return ARITH_FP32_PIR;
+    default: return ARITH_FP32_P64;
+  }
+}
 
 // Stage launchers.  Each (arithmetic, feature set, order) combination is
 // compiled separately from dg_stage_inst.cu (build flags select it), so the
@@ -48,6 +59,7 @@ cudaError_t launch_stage_p(int mode, int block, const void* params, cudaStream_t
   cudaError_t DGSWE_DIAG_NAME(SUFFIX, P)(const Mesh& m, const void* w, const void* hb, double det, double gg, \
                                          double* partial, cudaStream_t s);
 #define DGSWE_DECLARE_AUX_ALL(SUFFIX) \
+  DGSWE_DECLARE_AUX_P(SUFFIX, 0)      \
   DGSWE_DECLARE_AUX_P(SUFFIX, 1)      \
   DGSWE_DECLARE_AUX_P(SUFFIX, 2)      \
   DGSWE_DECLARE_AUX_P(SUFFIX, 3)      \
@@ -56,6 +68,7 @@ DGSWE_DECLARE_AUX_ALL(fp64)
 DGSWE_DECLARE_AUX_ALL(fp32p64)
 DGSWE_DECLARE_AUX_ALL(fp32p32)
 DGSWE_DECLARE_AUX_ALL(fp32pdf)
+DGSWE_DECLARE_AUX_ALL(fp32pir)
 
 template <int P, class REAL>
 cudaError_t launch_static_p(const Mesh& m, double gg, const double* hb64, void* hb, void* hbt, void* ghb, void* lin,
@@ -74,6 +87,7 @@ cudaError_t launch_diag_p(const Mesh& m, const void* w, const void* hb, double d
 }
 
 #define DGSWE_DECLARE_STAGE_ALL(SUFFIX) \
+  DGSWE_DECLARE_STAGE_P(SUFFIX, 0)      \
   DGSWE_DECLARE_STAGE_P(SUFFIX, 1)      \
   DGSWE_DECLARE_STAGE_P(SUFFIX, 2)      \
   DGSWE_DECLARE_STAGE_P(SUFFIX, 3)      \
@@ -82,6 +96,7 @@ DGSWE_DECLARE_STAGE_ALL(fp64)
 DGSWE_DECLARE_STAGE_ALL(fp32p64)
 DGSWE_DECLARE_STAGE_ALL(fp32p32)
 DGSWE_DECLARE_STAGE_ALL(fp32pdf)
+DGSWE_DECLARE_STAGE_ALL(fp32pir)
 DGSWE_DECLARE_STAGE_ALL(fp64_gen)
 DGSWE_DECLARE_STAGE_ALL(fp32p64_gen)
 DGSWE_DECLARE_STAGE_ALL(fp32p32_gen)
@@ -90,6 +105,7 @@ cudaError_t stage_fp64(int p, int mode, int block, const void* params, cudaStrea
 cudaError_t stage_fp32p64(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p32(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32pdf(int p, int mode, int block, const void* params, cudaStream_t s);
+cudaError_t stage_fp32pir(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp64_gen(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p64_gen(int p, int mode, int block, const void* params, cudaStream_t s);
 cudaError_t stage_fp32p32_gen(int p, int mode, int block, const void* params, cudaStream_t s);
@@ -102,6 +118,8 @@ cudaError_t static_fp32p64(int p, const Mesh& m, double g, const double* hb64, v
 cudaError_t static_fp32p32(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
                            void* lin, cudaStream_t s);
 cudaError_t static_fp32pdf(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
+                           void* lin, cudaStream_t s);
+cudaError_t static_fp32pir(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
                            void* lin, cudaStream_t s);
 
 // fill the derived geometry of a uniform mesh
@@ -128,6 +146,8 @@ cudaError_t diag_fp32p64(int p, const Mesh& m, const void* w, const void* hb, do
 cudaError_t diag_fp32p32(int p, const Mesh& m, const void* w, const void* hb, double det, double g,
                          double* partial, cudaStream_t s);
 cudaError_t diag_fp32pdf(int p, const Mesh& m, const void* w, const void* hb, double det, double g,
+                         double* partial, cudaStream_t s);
+cudaError_t diag_fp32pir(int p, const Mesh& m, const void* w, const void* hb, double det, double g,
                          double* partial, cudaStream_t s);
 
 }  // namespace dgswe

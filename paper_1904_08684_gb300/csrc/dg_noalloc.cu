@@ -65,16 +65,18 @@ template <class Real>
 dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d_in, void* d_out,
               cudaStream_t s) {
   const int P = cfg->p;
-  const int K = (P + 1) * (P + 2) / 2, K1 = P * (P + 1) / 2, P1 = P + 1, NREC = 6 * P1 + 1;
+  const int K = (P + 1) * (P + 2) / 2, P1 = P + 1, NREC = 6 * P1 + 1;
+  // bathymetry space P^max(p,1): basis size, edge modes, gradient basis
+  const int PB = P > 0 ? P : 1, KB = (PB + 1) * (PB + 2) / 2, PB1 = PB + 1, KB1 = PB * (PB + 1) / 2;
   const long long E = 2LL * cfg->nx * cfg->ny;
   const size_t rs = sizeof(Real);
   // carve the array: error word, hb, hb traces, hb gradients, vs, records,
   // and in FP64 the matrices of the terms linear in xi
   const size_t o_err = 0;
   const size_t o_hb = o_err + round_up(sizeof(unsigned));
-  const size_t o_hbt = o_hb + round_up((size_t)K * E * rs);
-  const size_t o_ghb = o_hbt + round_up((size_t)3 * P1 * E * rs);
-  const size_t o_vs = o_ghb + round_up((size_t)2 * K1 * E * rs);
+  const size_t o_hbt = o_hb + round_up((size_t)KB * E * rs);
+  const size_t o_ghb = o_hbt + round_up((size_t)3 * PB1 * E * rs);
+  const size_t o_vs = o_ghb + round_up((size_t)2 * KB1 * E * rs);
   const size_t o_rec = o_vs + round_up((size_t)3 * K * E * rs);
   const size_t o_lin = o_rec + round_up((size_t)3 * NREC * E * rs);
   const bool fp64 = arith == ARITH_FP64;
@@ -94,6 +96,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
     case ARITH_FP64: e = static_fp64(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, lin, s); break;
     case ARITH_FP32_P64: e = static_fp32p64(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
     case ARITH_FP32_PDF: e = static_fp32pdf(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
+    case ARITH_FP32_PIR: e = static_fp32pir(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
     default: e = static_fp32p32(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
   }
   if (e != cudaSuccess) return DG_ERR_CUDA;
@@ -120,6 +123,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
       case ARITH_FP64: return stage_fp64(P, mode, block, &sp, s);
       case ARITH_FP32_P64: return stage_fp32p64(P, mode, block, &sp, s);
       case ARITH_FP32_PDF: return stage_fp32pdf(P, mode, block, &sp, s);
+      case ARITH_FP32_PIR: return stage_fp32pir(P, mode, block, &sp, s);
       default: return stage_fp32p32(P, mode, block, &sp, s);
     }
   };
@@ -136,9 +140,9 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
 extern "C" dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_state_in,
                                     void* d_rhs_out, void* stream) {
   if (!cfg || !d_hb || !d_state_in || !d_rhs_out || d_state_in == d_rhs_out) return DG_ERR_ARG;
-  if (cfg->nx < 1 || cfg->ny < 1 || cfg->p < 1 || cfg->p > 4 || !(cfg->Lx > 0.0) || !(cfg->Ly > 0.0) ||
+  if (cfg->nx < 1 || cfg->ny < 1 || cfg->p < 0 || cfg->p > 4 || !(cfg->Lx > 0.0) || !(cfg->Ly > 0.0) ||
       !(cfg->g > 0.0) || cfg->vertex_xy || cfg->bc < 0 || cfg->bc > 1 || cfg->precision < 0 ||
-      cfg->precision > 1 || cfg->proj_precision < 0 || cfg->proj_precision > 2)
+      cfg->precision > 1 || cfg->proj_precision < 0 || cfg->proj_precision > 3)
     return DG_ERR_ARG;
   if (cfg->bc == DG_BC_PERIODIC && (cfg->nx < 2 || cfg->ny < 2)) return DG_ERR_ARG;
   if (cfg->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
@@ -147,10 +151,7 @@ extern "C" dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, cons
   if (cfg->block_size != 0 && (cfg->block_size < 32 || cfg->block_size > 128 || cfg->block_size % 32))
     return DG_ERR_ARG;
   if (2.0 * (double)cfg->nx * (double)cfg->ny > 1.0e8) return DG_ERR_ARG;
-  const int arith = cfg->precision == DG_PREC_FP64
-                        ? ARITH_FP64
-                        : (cfg->proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32
-                                                 : cfg->proj_precision == DG_PROJ_DF64 ? ARITH_FP32_PDF : ARITH_FP32_P64);
+  const int arith = arith_of(cfg->precision, cfg->proj_precision);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (arith == ARITH_FP64) return run<double>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, s);
   return run<float>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, s);

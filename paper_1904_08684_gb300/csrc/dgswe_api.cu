@@ -25,6 +25,7 @@ struct GraphSlot {
 struct dg_ctx {
   dg_config cfg;
   int P, K, K1, P1, NREC;
+  int KB, PB1, KB1;        // bathymetry space P^max(p,1): basis, edge modes, gradient basis
   long long E;
   int arith;
   size_t rsz;  // bytes per Real
@@ -37,8 +38,8 @@ struct dg_ctx {
   void* vs[2];           // volume+source integrals of the evaluated state
   void* rec[2];          // side records of the evaluated state
   void* hb;              // [K][E]
-  void* hbt;             // [3][P1][E]
-  void* ghb;             // [2][K1][E]
+  void* hbt;             // [3][PB1][E]
+  void* ghb;             // [2][KB1][E]
   void* lin;             // FP64 only: [2][K][K][E] terms linear in xi
   double* geo;           // general meshes: [NGEO][E] per-element geometry
   double* vq;            // forcing: volume Gauss rule [3][nqv]
@@ -59,6 +60,8 @@ struct dg_ctx {
 namespace {
 
 int K_of(int p) { return (p + 1) * (p + 2) / 2; }
+// basis size of the bathymetry space P^max(p,1)
+int KB_of(int p) { return K_of(p > 1 ? p : 1); }
 
 dg_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return DG_OK;
@@ -78,19 +81,21 @@ dg_status validate(const dg_config* c) {
   if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
   if (c->rk_order < 1 || c->rk_order > 3) return DG_ERR_ARG;
   if (c->bc < 0 || c->bc > 2 || c->precision < 0 || c->precision > 1) return DG_ERR_ARG;
-  if (c->proj_precision < 0 || c->proj_precision > 2) return DG_ERR_ARG;
+  if (c->proj_precision < 0 || c->proj_precision > 3) return DG_ERR_ARG;
   if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
   if (!(c->tau_bf >= 0.0) || !std::isfinite(c->tau_bf) || !std::isfinite(c->f_c)) return DG_ERR_ARG;
   // the stage kernels are compiled for at most 128 threads per block
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 128 || c->block_size % 32)) return DG_ERR_ARG;
   if (c->bc == DG_BC_PERIODIC && (c->nx < 2 || c->ny < 2)) return DG_ERR_ARG;
   if (c->forcing < 0 || c->forcing > 1) return DG_ERR_ARG;
-  if (c->p == 0) return DG_ERR_UNSUPPORTED;
   if (c->bc == DG_BC_DIRICHLET && c->forcing != DG_FORCING_MANUFACTURED) return DG_ERR_UNSUPPORTED;
   if (c->vertex_xy && c->bc == DG_BC_PERIODIC) return DG_ERR_UNSUPPORTED;
-  if (c->precision == DG_PREC_FP32_MIXED && c->proj_precision == DG_PROJ_DF64 &&
-      (c->p > 3 || c->vertex_xy || c->forcing != DG_FORCING_NONE || c->bc == DG_BC_DIRICHLET))
+  // the double-float and mixed solves are built for uniform meshes without
+  // forcing (double-float: p <= 3)
+  if (c->precision == DG_PREC_FP32_MIXED && (c->proj_precision == DG_PROJ_DF64 || c->proj_precision == DG_PROJ_MIXED) &&
+      (c->vertex_xy || c->forcing != DG_FORCING_NONE || c->bc == DG_BC_DIRICHLET))
     return DG_ERR_UNSUPPORTED;
+  if (c->precision == DG_PREC_FP32_MIXED && c->proj_precision == DG_PROJ_DF64 && c->p > 3) return DG_ERR_UNSUPPORTED;
   if (2.0 * (double)c->nx * (double)c->ny > 4.0e9) return DG_ERR_ARG;
   return DG_OK;
 }
@@ -103,6 +108,7 @@ cudaError_t launch_stage_any(const dg_ctx* c, int mode, const void* params, cuda
     case ARITH_FP64: return (gen ? stage_fp64_gen : stage_fp64)(c->P, mode, block, params, s);
     case ARITH_FP32_P64: return (gen ? stage_fp32p64_gen : stage_fp32p64)(c->P, mode, block, params, s);
     case ARITH_FP32_PDF: return stage_fp32pdf(c->P, mode, block, params, s);
+    case ARITH_FP32_PIR: return stage_fp32pir(c->P, mode, block, params, s);
     default: return (gen ? stage_fp32p32_gen : stage_fp32p32)(c->P, mode, block, params, s);
   }
 }
@@ -263,10 +269,6 @@ __global__ void cvt_kernel_f(const double* __restrict__ a, float* __restrict__ b
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = float(a[i]);
 }
-__global__ void cvt_kernel_b(const float* __restrict__ a, double* __restrict__ b, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = double(a[i]);
-}
 
 // FP64 element-major [F][E][K] <-> context-precision SoA [F][K][E] on the device
 template <class Real>
@@ -294,16 +296,6 @@ dg_status store_real(const dg_ctx* c, const double* src, void* dst, long long n,
   }
   return DG_OK;
 }
-dg_status load_real(const dg_ctx* c, const void* src, double* dst, long long n, cudaStream_t s) {
-  if (c->arith == ARITH_FP64) {
-    CK(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-  } else if (n > 0) {
-    cvt_kernel_b<<<(unsigned)((n + 255) / 256), 256, 0, s>>>((const float*)src, dst, n);
-    CK(cudaGetLastError());
-  }
-  return DG_OK;
-}
-
 void free_ctx(dg_ctx* c) {
   if (!c) return;
   for (auto& row : c->graph)
@@ -447,10 +439,11 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   c->K1 = K_of(cfg->p - 1);
   c->P1 = cfg->p + 1;
   c->NREC = 6 * c->P1 + 1;
+  c->KB = KB_of(cfg->p);
+  c->PB1 = std::max(cfg->p, 1) + 1;
+  c->KB1 = K_of(std::max(cfg->p, 1) - 1);
   c->E = 2LL * cfg->nx * cfg->ny;
-  c->arith = cfg->precision == DG_PREC_FP64 ? ARITH_FP64
-                                            : (cfg->proj_precision == DG_PROJ_FP32 ? ARITH_FP32_P32
-                                                 : cfg->proj_precision == DG_PROJ_DF64 ? ARITH_FP32_PDF : ARITH_FP32_P64);
+  c->arith = arith_of(cfg->precision, cfg->proj_precision);
   c->rsz = c->arith == ARITH_FP64 ? sizeof(double) : sizeof(float);
   c->stream = (cudaStream_t)stream;
   const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
@@ -482,9 +475,9 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
     alloc(&c->vs[i], st);
     alloc(&c->rec[i], (size_t)3 * c->NREC * E * c->rsz);
   }
-  alloc(&c->hb, (size_t)c->K * E * c->rsz);
-  alloc(&c->hbt, (size_t)3 * c->P1 * E * c->rsz);
-  alloc(&c->ghb, (size_t)2 * c->K1 * E * c->rsz);
+  alloc(&c->hb, (size_t)c->KB * E * c->rsz);
+  alloc(&c->hbt, (size_t)3 * c->PB1 * E * c->rsz);
+  alloc(&c->ghb, (size_t)2 * c->KB1 * E * c->rsz);
   if (c->arith == ARITH_FP64) alloc(&c->lin, (size_t)2 * c->K * c->K * E * c->rsz);
   if (!geo_h.empty()) alloc((void**)&c->geo, sizeof(double) * geo_h.size());
   std::vector<double> vq_h, eq_h;
@@ -533,6 +526,9 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
     case ARITH_FP32_PDF:
       le = static_fp32pdf(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss);
       break;
+    case ARITH_FP32_PIR:
+      le = static_fp32pir(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss);
+      break;
     default: le = static_fp32p32(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss); break;
   }
   if (le == cudaSuccess) le = cudaStreamSynchronize(ss);
@@ -550,6 +546,8 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
 extern "C" {
 
 int dg_num_basis(int p) { return (p < 0 || p > 4) ? 0 : K_of(p); }
+
+int dg_num_basis_bathymetry(int p) { return (p < 0 || p > 4) ? 0 : KB_of(p); }
 
 long long dg_num_elements(const dg_config* cfg) {
   if (!cfg || cfg->nx < 1 || cfg->ny < 1) return 0;
@@ -584,16 +582,17 @@ dg_status dg_init(const dg_config* cfg, const double* hb, const double* xi, cons
   dg_status s = validate(cfg);
   if (s != DG_OK) return s;
   if (!hb || !xi || !qx || !qy || !out) return DG_ERR_ARG;
-  const int K = K_of(cfg->p);
+  const int K = K_of(cfg->p), KB = KB_of(cfg->p);
   const long long E = 2LL * cfg->nx * cfg->ny;
   double* tmp = nullptr;
-  cudaError_t e = cudaMalloc(&tmp, sizeof(double) * 4 * (size_t)K * E);
+  cudaError_t e = cudaMalloc(&tmp, sizeof(double) * (size_t)(KB + 3 * K) * E);
   if (e != cudaSuccess) return cuda_status(e);
   cudaStream_t ss = (cudaStream_t)stream;
+  // layout of tmp: h_b [KB][E], then xi, qx, qy [K][E] each
+  double* dst[4] = {tmp, tmp + (size_t)KB * E, tmp + (size_t)(KB + K) * E, tmp + (size_t)(KB + 2 * K) * E};
   const double* src[4] = {hb, xi, qx, qy};
-  for (int f = 0; f < 4 && s == DG_OK; ++f) s = upload_soa(src[f], E, K, tmp + (size_t)f * K * E, ss);
-  if (s == DG_OK)
-    s = create(cfg, tmp, tmp + (size_t)K * E, tmp + 2 * (size_t)K * E, tmp + 3 * (size_t)K * E, stream, out);
+  for (int f = 0; f < 4 && s == DG_OK; ++f) s = upload_soa(src[f], E, f == 0 ? KB : K, dst[f], ss);
+  if (s == DG_OK) s = create(cfg, dst[0], dst[1], dst[2], dst[3], stream, out);
   cudaStreamSynchronize(ss);
   cudaFree(tmp);
   return s;
@@ -732,6 +731,9 @@ dg_status dg_diagnostics(dg_ctx* c, double* mass, double* energy) {
       break;
     case ARITH_FP32_PDF:
       e = diag_fp32pdf(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream);
+      break;
+    case ARITH_FP32_PIR:
+      e = diag_fp32pir(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream);
       break;
     default: e = diag_fp32p32(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream); break;
   }

@@ -201,7 +201,7 @@ def main(out):
     parts = ["// Generated by gen_tables.py (exact rational arithmetic); do not edit.\n",
              "#pragma once\n\nnamespace dgswe {\n\ntemplate <int P> struct RefTables;\n\n"]
     counts = []
-    for p in range(1, PMAX + 1):
+    for p in range(0, PMAX + 1):
         K, P1, T, S, R, Lam, Lpt = tables_for(p, basis, leg)
         nnz = lambda a: sum(1 for x in _flat(a) if x != 0.0)  # noqa: E731
         counts.append((p, nnz(T), nnz(S[0]), nnz(S[1]), nnz(R), nnz(Lam)))

@@ -72,10 +72,12 @@ def _gpu_rhs(cfg, hb, xi, U, V, dtype=torch.float64):
 
 
 # ------------------------------------------------------------------ RHS
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("bc", ["periodic", "reflective"])
 def test_rhs_matches_oracle_fp64(oracle_mod, p, bc):
-    """13 x 11 quads = 286 triangles: several 128-thread blocks and a ragged tail."""
+    """13 x 11 quads = 286 triangles: several 128-thread blocks and a ragged
+    tail.  p = 0 is the degenerate case: a first-order finite-volume
+    Lax-Friedrichs scheme, with h_b in P^1 (source and edge depths)."""
     wl = I.waves_p2_512(n=13, p=p, ngauss=3)
     wl.ny = 11
     wl.bc = bc
@@ -92,13 +94,14 @@ def test_rhs_matches_oracle_fp64(oracle_mod, p, bc):
         assert np.abs(got[f] - ref[f]).max() <= tol * scale, (f, np.abs(got[f] - ref[f]).max() / scale)
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4])
-@pytest.mark.parametrize("proj", ["fp64", "fp32", "df64"])
+@pytest.mark.parametrize("p", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("proj", ["fp64", "fp32", "df64", "mixed"])
 def test_rhs_fp32_state(oracle_mod, p, proj):
-    """FP32 state and contractions (velocity solve in FP64, FP32 or
-    double-float): the RHS agrees with the FP64 oracle to FP32 round-off
-    amplified by the Lax-Friedrichs jump term (|jump| ~ eps |w|, times
-    lambda / h).  The double-float solve is built for p <= 3."""
+    """FP32 state and contractions (velocity solve in FP64, FP32,
+    double-float, or FP32 with FP64-residual refinement): the RHS agrees with
+    the FP64 oracle to FP32 round-off amplified by the Lax-Friedrichs jump
+    term (|jump| ~ eps |w|, times lambda / h).  The double-float solve is
+    built for p <= 3."""
     if proj == "df64" and p > 3:
         pytest.skip("double-float solve is built for p <= 3")
     wl = I.waves_p2_512(n=13, p=p, ngauss=3)
@@ -142,7 +145,7 @@ def test_run_matches_oracle_hump_p1(oracle_mod):
         assert _relL2(g_, r_) <= 1e-12
 
 
-@pytest.mark.parametrize("p", [2, 3])
+@pytest.mark.parametrize("p", [0, 2, 3])
 def test_run_matches_oracle_waves(oracle_mod, p):
     """periodic waves on sinusoidal bathymetry with a mean flow, SSP-RK3."""
     wl = I.waves_p2_512(n=16, p=p, ngauss=4)
@@ -182,7 +185,7 @@ def test_fixed_dt_rk1_step(oracle_mod):
 
 # ------------------------------------------------------------------ FP32 state
 @pytest.mark.slow
-@pytest.mark.parametrize("proj", ["fp64", "df64"])
+@pytest.mark.parametrize("proj", ["fp64", "df64", "mixed"])
 def test_fp32_mixed_hump_p3_1000_steps(oracle_mod, proj):
     """FP32 state and contractions, FP64 (or double-float) velocity solve,
     p = 3, 1000 SSP-RK3 steps against the FP64 oracle: relative L2 per field

@@ -45,6 +45,8 @@ def test_counts_and_status_strings(lib):
     from paper_1904_08684_gb300 import binding as B
     assert [B.dg_num_basis(p) for p in range(5)] == [1, 3, 6, 10, 15]
     assert B.dg_num_basis(5) == 0
+    # h_b lives in P^max(p,1)
+    assert [B.dg_num_basis_bathymetry(p) for p in range(6)] == [3, 3, 6, 10, 15, 0]
     assert B.dg_num_elements(B.make_config(7, 5, 2)) == 70
     assert B.dg_proj_num_nodes(2) == 25
     assert B.dg_status_str(B.DG_ERR_DRY) == "DG_ERR_DRY"
@@ -75,7 +77,7 @@ def test_invalid_configs_rejected_without_gpu(lib, bad):
 def test_unsupported_configs(lib):
     import numpy as np
     from paper_1904_08684_gb300 import binding as B
-    for kw in (dict(p=0), dict(bc="dirichlet"), dict(bc="periodic", vertex_xy=np.zeros((25, 2)))):
+    for kw in (dict(bc="dirichlet"), dict(bc="periodic", vertex_xy=np.zeros((25, 2)))):
         base = dict(nx=4, ny=4, p=1, bc="periodic")
         base.update(kw)
         cfg = B.make_config(**base)
@@ -96,9 +98,10 @@ def test_batch_rejects_mixed_or_unsupported_without_gpu(lib):
     with pytest.raises(B.DGError) as ei:
         B.dg_batch_init([a, b], one, one, one, one)
     assert ei.value.status == B.DG_ERR_ARG
-    with pytest.raises(B.DGError) as ei:
-        B.dg_batch_init([c], [1], [1], [1], [1])
-    assert ei.value.status == B.DG_ERR_UNSUPPORTED
+    for unsupported in (c, B.make_config(4, 4, 0)):      # the batched kernel holds p = 1..3
+        with pytest.raises(B.DGError) as ei:
+            B.dg_batch_init([unsupported], [1], [1], [1], [1])
+        assert ei.value.status == B.DG_ERR_UNSUPPORTED
     with pytest.raises(B.DGError) as ei:
         B.dg_batch_init([], [], [], [], [])
     assert ei.value.status == B.DG_ERR_ARG
