@@ -993,13 +993,15 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
   const bool full_G = FEAT && sp.m.geo != nullptr;   // off-diagonal terms vanish on the uniform mesh
   sfor<0, K>([&](auto a) {
     constexpr int aa = CV(a);
-    Real v0 = G11 * sdot_row<P, 0, aa>(U) + G22 * sdot_row<P, 1, aa>(V);
-    Real v1 = G11 * sdot_row<P, 0, aa>(FxU) + G22 * sdot_row<P, 1, aa>(Puv);
-    Real v2 = G11 * sdot_row<P, 0, aa>(Pvu) + G22 * sdot_row<P, 1, aa>(FyV);
+    // explicit fused forms: a contracted a*b + c*d could fuse either product,
+    // and the choice would depend on the kernel the code is compiled into
+    Real v0 = fma(G11, sdot_row<P, 0, aa>(U), G22 * sdot_row<P, 1, aa>(V));
+    Real v1 = fma(G11, sdot_row<P, 0, aa>(FxU), G22 * sdot_row<P, 1, aa>(Puv));
+    Real v2 = fma(G11, sdot_row<P, 0, aa>(Pvu), G22 * sdot_row<P, 1, aa>(FyV));
     if (full_G) {
-      v0 += G12 * sdot_row<P, 1, aa>(U) + G21 * sdot_row<P, 0, aa>(V);
-      v1 += G12 * sdot_row<P, 1, aa>(FxU) + G21 * sdot_row<P, 0, aa>(Puv);
-      v2 += G12 * sdot_row<P, 1, aa>(Pvu) + G21 * sdot_row<P, 0, aa>(FyV);
+      v0 += fma(G12, sdot_row<P, 1, aa>(U), G21 * sdot_row<P, 0, aa>(V));
+      v1 += fma(G12, sdot_row<P, 1, aa>(FxU), G21 * sdot_row<P, 0, aa>(Puv));
+      v2 += fma(G12, sdot_row<P, 1, aa>(Pvu), G21 * sdot_row<P, 0, aa>(FyV));
     }
     if constexpr (kLin) {
       sfor<0, K>([&](auto k) {
@@ -1032,7 +1034,7 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
   if (sp.lam_next) {
     const double Hm = double(H[0]);
     const double um = double(U[0]) / Hm, vm = double(V[0]) / Hm;
-    lam_e = sqrt(um * um + vm * vm) + sqrt(double(sp.g) * 1.4142135623730951 * Hm);
+    lam_e = sqrt(fma(um, um, vm * vm)) + sqrt(double(sp.g) * 1.4142135623730951 * Hm);
   }
   return lam_e;
 }

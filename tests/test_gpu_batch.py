@@ -42,7 +42,8 @@ def _gpu():
     B.load()
 
 
-@pytest.mark.parametrize("precision,proj", [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32"), ("fp32", "df64")])
+@pytest.mark.parametrize("precision,proj", [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32"), ("fp32", "df64"),
+                                             ("fp32", "mixed")])
 def test_batch_equals_single_contexts(precision, proj):
     """the batched persistent kernel reproduces single contexts bit for bit"""
     inst = [_instance(k, *s, precision, proj) for k, s in enumerate(SPECS)]
