@@ -26,6 +26,7 @@ struct BatchInst {
   const void* hbt;
   const void* ghb;
   const void* lin;     // FP64 batches: [2][K][K][E], else null
+  const double* ahb;   // mixed-solve batches: [K(K+1)/2][E], else null
   double* lam;         // slot s of this instance at lam[s * n_inst]
   double* t;
   int p;
@@ -66,6 +67,7 @@ __global__ void __launch_bounds__(128, (stage_min_blocks<3, Real>())) batch_kern
     sp.hbt = static_cast<const Real*>(d.hbt);
     sp.ghb = static_cast<const Real*>(d.ghb);
     sp.lin = static_cast<const Real*>(d.lin);
+    sp.ahb = d.ahb;
     sp.inv_det = d.inv_det;
     sp.det = d.det;
     sp.tau_bf = d.tau_bf;

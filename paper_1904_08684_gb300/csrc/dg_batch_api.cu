@@ -38,7 +38,7 @@ struct HostInst {
   dg_config cfg;
   int p, K, K1, P1, NREC;
   long long E;
-  size_t o_state, o_rec, o_hb, o_hbt, o_ghb, o_lin;  // byte offsets in the arenas
+  size_t o_state, o_rec, o_hb, o_hbt, o_ghb, o_lin, o_ahb;  // byte offsets in the arenas
 };
 
 }  // namespace
@@ -59,6 +59,7 @@ struct dg_batch {
   void* hbt = nullptr;
   void* ghb = nullptr;
   void* lin = nullptr;          // FP64 batches only
+  void* ahb = nullptr;          // mixed-solve batches only
   double* lam = nullptr;        // [2][n]
   double* t = nullptr;          // [n]
   unsigned* err = nullptr;
@@ -194,7 +195,7 @@ void free_batch(dg_batch* b) {
   if (!b) return;
   drop_graphs(b);
   void* bufs[] = {b->w[0], b->w[1], b->w[2], b->vs[0], b->vs[1], b->rec[0], b->rec[1], b->hb, b->hbt,
-                  b->ghb, b->lin, b->lam, b->t, b->err, b->counters, b->d_inst, b->d_items};
+                  b->ghb, b->lin, b->ahb, b->lam, b->t, b->err, b->counters, b->d_inst, b->d_items};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -256,7 +257,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   b->S = cfgs[0].rk_order;
   b->adaptive = !(cfgs[0].dt > 0.0);
   b->stream = (cudaStream_t)stream;
-  size_t ost = 0, orec = 0, ohb = 0, ohbt = 0, oghb = 0, olin = 0;
+  size_t ost = 0, orec = 0, ohb = 0, ohbt = 0, oghb = 0, olin = 0, oahb = 0;
   b->dofs = 0;
   for (int i = 0; i < n; ++i) {
     HostInst h;
@@ -273,12 +274,14 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     h.o_hbt = ohbt;
     h.o_ghb = oghb;
     h.o_lin = olin;
+    h.o_ahb = oahb;
     ost += align256((size_t)3 * h.K * h.E * b->rsz);
     orec += align256((size_t)3 * h.NREC * h.E * b->rsz);
     ohb += align256((size_t)h.K * h.E * b->rsz);
     ohbt += align256((size_t)3 * h.P1 * h.E * b->rsz);
     oghb += align256((size_t)2 * h.K1 * h.E * b->rsz);
     if (b->arith == ARITH_FP64) olin += align256((size_t)2 * h.K * h.K * h.E * b->rsz);
+    if (b->arith == ARITH_FP32_PIR) oahb += align256(sizeof(double) * tri_size(h.K) * h.E);
     b->dofs += 3LL * h.K * h.E;
     b->inst.push_back(h);
   }
@@ -299,6 +302,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   alloc(&b->hbt, ohbt);
   alloc(&b->ghb, oghb);
   if (olin) alloc(&b->lin, olin);
+  if (oahb) alloc(&b->ahb, oahb);
   alloc((void**)&b->lam, sizeof(double) * 2 * n);
   alloc((void**)&b->t, sizeof(double) * n);
   alloc((void**)&b->err, sizeof(unsigned));
@@ -340,6 +344,7 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     d.hbt = (char*)b->hbt + h.o_hbt;
     d.ghb = (char*)b->ghb + h.o_ghb;
     d.lin = b->lin ? (char*)b->lin + h.o_lin : nullptr;
+    d.ahb = b->ahb ? (const double*)((char*)b->ahb + h.o_ahb) : nullptr;
     d.lam = b->lam + i;
     d.t = b->t + i;
     d.p = h.p;
@@ -354,7 +359,10 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
       case ARITH_FP64: e = static_fp64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, pl, s); break;
       case ARITH_FP32_P64: e = static_fp32p64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
       case ARITH_FP32_PDF: e = static_fp32pdf(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
-      case ARITH_FP32_PIR: e = static_fp32pir(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
+      case ARITH_FP32_PIR:
+        e = static_fp32pir(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s);
+        if (e == cudaSuccess) e = static_ahb(h.p, d.m, hbi, (double*)d.ahb, s);
+        break;
       default: e = static_fp32p32(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
     }
   }

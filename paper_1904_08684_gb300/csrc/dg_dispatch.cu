@@ -83,6 +83,20 @@ DGSWE_AUX_DISPATCH(fp32p32)
 DGSWE_AUX_DISPATCH(fp32pdf)
 DGSWE_AUX_DISPATCH(fp32pir)
 
+// static FP64 bathymetry matrix of the mixed solve
+cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, double* ahb, cudaStream_t s) {
+  const unsigned g = (unsigned)((m.E + 127) / 128);
+  switch (p) {
+    case 0: ahb_kernel<0><<<g, 128, 0, s>>>(m.E, hb64, ahb); break;
+    case 1: ahb_kernel<1><<<g, 128, 0, s>>>(m.E, hb64, ahb); break;
+    case 2: ahb_kernel<2><<<g, 128, 0, s>>>(m.E, hb64, ahb); break;
+    case 3: ahb_kernel<3><<<g, 128, 0, s>>>(m.E, hb64, ahb); break;
+    case 4: ahb_kernel<4><<<g, 128, 0, s>>>(m.E, hb64, ahb); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 // batched persistent kernel: mode 0 = evaluation, 1 = stage
 DGSWE_BATCH_DISPATCH(fp64)
 DGSWE_BATCH_DISPATCH(fp32p64)

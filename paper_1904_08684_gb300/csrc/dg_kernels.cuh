@@ -562,25 +562,34 @@ __device__ __forceinline__ void ldlt_solve(const PR (&L)[RefTables<P>::K][RefTab
 }
 
 // Marker type of the mixed-precision solve (FP32 state only): LDL^T and both
-// triangular solves in FP32, then one step of iterative refinement with the
-// residual r = b - A x0 formed in FP64 (A assembled entry by entry in FP64
-// and used at once), x = x0 + A^{-1} r with the FP32 factors (Wilkinson's
-// mixed-precision refinement).  With kappa(A) * K * 2^-24 << 1 the result is
-// the FP64 solution to within FP32 rounding; elements whose FP32 pivots
-// spread over more than 2^10 (kappa estimate), or fail, take the FP64 solve.
+// triangular solves in FP32, then one step of iterative refinement,
+// x = x0 + A^{-1} r with the FP32 factors (Wilkinson's mixed-precision
+// refinement), where the residual r = b - A x0 splits A = A_hb + A_xi:
+//   A_hb = sum_n T[n][a][b] h_b,n  is static, formed once in FP64 (ahb), and
+//          its product with x0 is accumulated in FP64;
+//   A_xi = sum_n T[n][a][b] xi_n   is formed and applied in FP32, whose
+//          rounding error, eps32 |A_xi| |x0| <= eps32 (|xi| / H) |b|, stays
+//          below the FP32 rounding of the result.
+// With kappa(A) K 2^-24 << 1 the result is the FP64 solution to within FP32
+// rounding; elements whose FP32 pivots fail or spread by more than 2^10
+// (kappa estimate) take the FP64 solve.
 struct MixedIR {};
 
 template <int P, class PR, class R>
 __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R* V, R* u, R* v);
 
+// number of entries of the lower triangle of a K x K matrix
+__host__ __device__ constexpr int tri_size(int K) { return K * (K + 1) / 2; }
+
 template <int P, class R>
-__device__ __forceinline__ bool project_velocity_ir(const R* H, const R* U, const R* V, R* u, R* v) {
+__device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, const R* U, const R* V, R* u, R* v,
+                                                    const double* __restrict__ ahb, long long E) {
   using Tb = RefTables<P>;
   constexpr int K = Tb::K;
   float L[K][K], Dg[K], rD[K];
   float Hf[K];
   sfor<0, K>([&](auto n) { Hf[CV(n)] = float(H[CV(n)]); });
-  bool ok = ldlt_factor<P, float>(Hf, L, Dg, rD);
+  const bool ok = ldlt_factor<P, float>(Hf, L, Dg, rD);
   float dmin = Dg[0], dmax = Dg[0];
   sfor<1, K>([&](auto j) {
     dmin = fminf(dmin, Dg[CV(j)]);
@@ -590,42 +599,50 @@ __device__ __forceinline__ bool project_velocity_ir(const R* H, const R* U, cons
   float u0[K], v0[K];
   ldlt_solve<P>(L, rD, U, u0);
   ldlt_solve<P>(L, rD, V, v0);
-  // residuals in FP64: A_ab = sum_n T[n][a][b] H_n, entry by entry
-  double Hd[K], ru[K], rv[K], ud[K], vd[K];
+  double ru[K], rv[K], ud[K], vd[K];
+  float su[K], sv[K];   // A_xi x0 in FP32
   sfor<0, K>([&](auto n) {
-    Hd[CV(n)] = double(H[CV(n)]);
     ru[CV(n)] = double(U[CV(n)]);
     rv[CV(n)] = double(V[CV(n)]);
     ud[CV(n)] = double(u0[CV(n)]);
     vd[CV(n)] = double(v0[CV(n)]);
+    su[CV(n)] = 0.f;
+    sv[CV(n)] = 0.f;
   });
   sfor<0, K>([&](auto aa) {
     constexpr int a = CV(aa);
     sfor<0, a + 1>([&](auto bb) {
       constexpr int b = CV(bb);
-      double A = 0.0;
+      const double Ah = ahb[(long long)(a * (a + 1) / 2 + b) * E];
+      ru[a] = fma(-Ah, ud[b], ru[a]);
+      rv[a] = fma(-Ah, vd[b], rv[a]);
+      if constexpr (a != b) {
+        ru[b] = fma(-Ah, ud[a], ru[b]);
+        rv[b] = fma(-Ah, vd[a], rv[b]);
+      }
+      float Ax = 0.f;
       bool any = false;
       sfor<0, K>([&](auto n) {
         constexpr double t = Tb::T[CV(n)][a][b];
         if constexpr (t != 0.0) {
-          A = fma(t, Hd[CV(n)], A);
+          Ax = fmaf(float(t), float(xi[CV(n)]), Ax);
           any = true;
         }
       });
       if (any) {
-        ru[a] = fma(-A, ud[b], ru[a]);
-        rv[a] = fma(-A, vd[b], rv[a]);
+        su[a] = fmaf(Ax, u0[b], su[a]);
+        sv[a] = fmaf(Ax, v0[b], sv[a]);
         if constexpr (a != b) {
-          ru[b] = fma(-A, ud[a], ru[b]);
-          rv[b] = fma(-A, vd[a], rv[b]);
+          su[b] = fmaf(Ax, u0[a], su[b]);
+          sv[b] = fmaf(Ax, v0[a], sv[b]);
         }
       }
     });
   });
   float rf[K], du[K], dv[K];
-  sfor<0, K>([&](auto i) { rf[CV(i)] = float(ru[CV(i)]); });
+  sfor<0, K>([&](auto i) { rf[CV(i)] = float(ru[CV(i)] - double(su[CV(i)])); });
   ldlt_solve<P>(L, rD, rf, du);
-  sfor<0, K>([&](auto i) { rf[CV(i)] = float(rv[CV(i)]); });
+  sfor<0, K>([&](auto i) { rf[CV(i)] = float(rv[CV(i)] - double(sv[CV(i)])); });
   ldlt_solve<P>(L, rD, rf, dv);
   // explicit rounding: the last solve step leaves u0 = y rD, and a
   // contracted y rD + du would depend on the compilation context
@@ -636,11 +653,37 @@ __device__ __forceinline__ bool project_velocity_ir(const R* H, const R* U, cons
   return true;
 }
 
+// A_hb of the mixed solve: FP64 sum_n T[n][a][b] h_b,n, n over the KB
+// bathymetry coefficients (P^max(p,1)), for b <= a
+template <int P>
+__global__ void ahb_kernel(long long E, const double* __restrict__ hb64, double* __restrict__ ahb) {
+  using D = Dims<P>;
+  using Tb = RefTables<D::PB>;
+  constexpr int K = D::K, KB = D::KB;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double h[KB];
+  sfor<0, KB>([&](auto i) { h[CV(i)] = hb64[CV(i) * E + e]; });
+  sfor<0, K>([&](auto aa) {
+    constexpr int a = CV(aa);
+    sfor<0, a + 1>([&](auto bb) {
+      constexpr int b = CV(bb);
+      double A = 0.0;
+      sfor<0, KB>([&](auto n) {
+        constexpr double t = Tb::T[CV(n)][a][b];
+        if constexpr (t != 0.0) A = fma(t, h[CV(n)], A);
+      });
+      ahb[(long long)(a * (a + 1) / 2 + b) * E + e] = A;
+    });
+  });
+}
+
 // Solve in precision PR (double, float, df64), or MixedIR (see above).
 template <int P, class PR, class R>
 __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R* V, R* u, R* v) {
   if constexpr (std::is_same<PR, MixedIR>::value) {
-    return project_velocity_ir<P>(H, U, V, u, v);
+    // callers without the static A_hb (diagnostics) take the FP64 solve
+    return project_velocity<P, double>(H, U, V, u, v);
   } else {
     using Tb = RefTables<P>;
     constexpr int K = Tb::K;
@@ -714,6 +757,8 @@ struct StageParams {
   const Real* ghb;    // [2][K1][E] det-scaled bathymetry gradient coefficients
   const Real* lin;    // FP64 only: [2][K][K][E] matrices of the terms linear in xi
                       // (g xi grad h_b source + g Pi(xi h_b) pressure part)
+  const double* ahb;  // mixed solve only: [K(K+1)/2][E] FP64 matrix A of the bathymetry,
+                      // sum_n T[n][a][b] h_b,n for b <= a (row-major lower triangle)
   // time step
   double dt_fixed;    // > 0: fixed step
   double cfl_num;     // cfl * d_min / (2p + 1)
@@ -932,7 +977,12 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
     hb[CV(i)] = sp.hb[CV(i) * E + e];
     H[CV(i)] = xi[CV(i)] + hb[CV(i)];
   });
-  if (!project_velocity<P, PR>(H, U, V, u, v)) err |= ERRF_DRY;
+  bool solved;
+  if constexpr (std::is_same<PR, MixedIR>::value)
+    solved = project_velocity_ir<P>(H, xi, U, V, u, v, sp.ahb + e, E);
+  else
+    solved = project_velocity<P, PR>(H, U, V, u, v);
+  if (!solved) err |= ERRF_DRY;
 
   // volume integrals (A~, grad phi_a) (Eqs. (15)-(16)): grad phi_a lies in
   // P^{p-1}, so only the first K1 coefficients of each projected product count

@@ -122,6 +122,9 @@ cudaError_t static_fp32pdf(int p, const Mesh& m, double g, const double* hb64, v
 cudaError_t static_fp32pir(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
                            void* lin, cudaStream_t s);
 
+// static FP64 bathymetry matrix of the mixed solve: ahb [K(K+1)/2][E]
+cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, double* ahb, cudaStream_t s);
+
 // fill the derived geometry of a uniform mesh
 inline Mesh make_mesh(int nx, int ny, double x0, double y0, double Lx, double Ly, bool periodic) {
   Mesh m;

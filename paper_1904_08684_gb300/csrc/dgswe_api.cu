@@ -41,6 +41,7 @@ struct dg_ctx {
   void* hbt;             // [3][PB1][E]
   void* ghb;             // [2][KB1][E]
   void* lin;             // FP64 only: [2][K][K][E] terms linear in xi
+  double* ahb;           // mixed solve only: [K(K+1)/2][E] FP64 bathymetry matrix
   double* geo;           // general meshes: [NGEO][E] per-element geometry
   double* vq;            // forcing: volume Gauss rule [3][nqv]
   double* eq;            // forcing: edge Gauss rule [nqe][7]
@@ -123,6 +124,7 @@ StageParams<Real> base_params(const dg_ctx* c) {
   sp.hbt = (const Real*)c->hbt;
   sp.ghb = (const Real*)c->ghb;
   sp.lin = (const Real*)c->lin;
+  sp.ahb = c->ahb;
   sp.forcing = c->cfg.forcing == DG_FORCING_MANUFACTURED;
   sp.dirichlet = c->cfg.bc == DG_BC_DIRICHLET;
   sp.t_now = c->scal + 2;
@@ -302,7 +304,7 @@ void free_ctx(dg_ctx* c) {
     for (auto& g : row)
       if (g.exec) cudaGraphExecDestroy(g.exec);
   void* bufs[] = {c->w[0], c->w[1], c->w[2], c->vs[0], c->vs[1], c->rec[0], c->rec[1], c->hb, c->hbt,
-                  c->ghb, c->lin, c->geo, c->vq, c->eq, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec,
+                  c->ghb, c->lin, c->ahb, c->geo, c->vq, c->eq, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec,
                   c->stage};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -479,6 +481,7 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   alloc(&c->hbt, (size_t)3 * c->PB1 * E * c->rsz);
   alloc(&c->ghb, (size_t)2 * c->KB1 * E * c->rsz);
   if (c->arith == ARITH_FP64) alloc(&c->lin, (size_t)2 * c->K * c->K * E * c->rsz);
+  if (c->arith == ARITH_FP32_PIR) alloc((void**)&c->ahb, sizeof(double) * tri_size(c->K) * E);
   if (!geo_h.empty()) alloc((void**)&c->geo, sizeof(double) * geo_h.size());
   std::vector<double> vq_h, eq_h;
   if (cfg->forcing == DG_FORCING_MANUFACTURED) {
@@ -528,6 +531,7 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
       break;
     case ARITH_FP32_PIR:
       le = static_fp32pir(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss);
+      if (le == cudaSuccess) le = static_ahb(c->P, c->mesh, d_hb, c->ahb, ss);
       break;
     default: le = static_fp32p32(c->P, c->mesh, cfg->g, d_hb, c->hb, c->hbt, c->ghb, nullptr, ss); break;
   }
