@@ -265,16 +265,26 @@ def run_batch(args, wls):
             e1.record(stream)
             torch.cuda.synchronize()
         ms, step_ms, value = reduce_time_and_value(e0.elapsed_time(e1), dofs * S, args.steps, world)
-        # end to end: copy every instance's state back to the host each step
+        # end to end through the public API with host buffers: per step every
+        # instance's state goes host -> device (dg_batch_set_state), one
+        # dg_batch_run step, and every state comes back (dg_batch_get_state)
+        host = [[torch.empty((wl.E, wl.K), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+                for wl in wls]
+        tcur = B.dg_batch_run(b, 0)
+        for i, wl in enumerate(wls):
+            B.dg_batch_get_state(b, i, wl.E, wl.K, out=host[i])
         n_e2e = max(1, min(args.steps, args.e2e_steps))
-        d2h = 0
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(n_e2e):
+            for i, wl in enumerate(wls):
+                B.dg_batch_set_state(b, i, *host[i], t=float(tcur[i]))
             B.dg_batch_run(b, 1)
             for i, wl in enumerate(wls):
-                B.dg_batch_get_state(b, i, wl.E, wl.K)
+                B.dg_batch_get_state(b, i, wl.E, wl.K, out=host[i])
         e2e_s = (time.perf_counter() - t0) / n_e2e
         d2h = sum(3 * wl.K * wl.E * 8 for wl in wls)
+        del host
     finally:
         B.dg_batch_destroy(b)
     launch_s = step_ms * 1e-3 / S
@@ -294,8 +304,9 @@ def run_batch(args, wls):
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
            "gpu_launches": S * args.steps, "roofline": roof,   # one persistent launch per stage
-           "e2e": {"value": dofs * S / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
-           "clocks": clk.summary(), "sim_time_range": [float(min(tvals)), float(max(tvals))]}
+           "e2e": {"value": dofs * S / e2e_s, "unit": UNIT, "h2d_bytes_per_step": d2h, "d2h_bytes_per_step": d2h},
+           "clocks": clk.summary(), "gpu": torch.cuda.get_device_name(local), "host_cores": os.cpu_count(),
+           "sim_time_range": [float(min(tvals)), float(max(tvals))]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         picks = [next(wl for wl in wls if wl.p == q) for q in (1, 2, 3) if any(w.p == q for w in wls)]
         parts = [cpu_baseline(wl, args.cpu_seconds / len(picks)) for wl in picks]
@@ -378,7 +389,7 @@ def run_ours(args):
            "roofline": roof,
            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": 3 * wl.K * wl.E * 8,
                    "d2h_bytes_per_step": 3 * wl.K * wl.E * 8},
-           "clocks": clk.summary(),
+           "clocks": clk.summary(), "gpu": torch.cuda.get_device_name(local), "host_cores": os.cpu_count(),
            "diagnostics": {"mass": mass, "energy": energy}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)

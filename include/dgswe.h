@@ -233,8 +233,15 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
  * instance's time.  Synchronises the stream once at the end. */
 dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out);
 
-/* state of instance i as host FP64 AoS [E_i][K_i] arrays (each may be NULL) */
+/* state of instance i as host FP64 AoS [E_i][K_i] arrays (each may be NULL;
+ * page-locked buffers make the copies faster).  Synchronises the stream. */
 dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy);
+
+/* replace the state of instance i (host FP64 AoS [E_i][K_i] arrays, all three
+ * required) and its model time t; the next dg_batch_run re-evaluates the
+ * batch.  Synchronises the stream.  Errors: DG_ERR_ARG, DG_ERR_OOM,
+ * DG_ERR_CUDA. */
+dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double* qx, const double* qy, double t);
 
 /* Autotuner: times trial_steps steps with 32, 64, 96 and 128 elements per
  * work item (one thread per element), restoring the state after each, and

@@ -26,8 +26,8 @@ PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
 EXPORTS = ["dg_num_basis", "dg_num_basis_bathymetry", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
            "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc",
-           "dg_batch_init", "dg_batch_run", "dg_batch_get_state", "dg_batch_autotune", "dg_batch_set_block",
-           "dg_batch_dofs", "dg_batch_destroy"]
+           "dg_batch_init", "dg_batch_run", "dg_batch_get_state", "dg_batch_set_state", "dg_batch_autotune",
+           "dg_batch_set_block", "dg_batch_dofs", "dg_batch_destroy"]
 
 
 class DGError(RuntimeError):
@@ -107,6 +107,7 @@ def load(build_if_missing=True):
     lib.dg_batch_init.argtypes = [ctypes.c_int, cp, vpp, vpp, vpp, vpp, vp, ctypes.POINTER(vp)]
     lib.dg_batch_run.argtypes = [vp, ctypes.c_int, dp]
     lib.dg_batch_get_state.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+    lib.dg_batch_set_state.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_double]
     lib.dg_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
     lib.dg_batch_set_block.argtypes = [vp, ctypes.c_int]
     lib.dg_batch_dofs.argtypes = [vp]
@@ -282,10 +283,21 @@ def dg_batch_run(b, nsteps):
     return t
 
 
-def dg_batch_get_state(b, i, E, K):
-    out = [np.zeros((E, K)) for _ in range(3)]
+def dg_batch_get_state(b, i, E, K, out=None):
+    """state of instance i as three host (E, K) FP64 arrays (written into
+    ``out`` if given, e.g. page-locked buffers)"""
+    if out is None:
+        out = [np.zeros((E, K)) for _ in range(3)]
+    for a in out:
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == E * K
     _check(load().dg_batch_get_state(b, int(i), *[_hptr(a) for a in out]), "dg_batch_get_state")
     return out
+
+
+def dg_batch_set_state(b, i, xi, qx, qy, t=0.0):
+    """replace the state (host (E, K) FP64 arrays) and time of instance i"""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (xi, qx, qy)]
+    _check(load().dg_batch_set_state(b, int(i), *[_hptr(a) for a in arrs], float(t)), "dg_batch_set_state")
 
 
 def dg_batch_autotune(b, trial_steps=2):

@@ -78,7 +78,8 @@ def _stale():
 
 
 def _headers():
-    return [os.path.join(CSRC, f) for f in ("dg_kernels.cuh", "dg_launch.cuh", "dg_batch.cuh", "gen_tables.py")] + \
+    return [os.path.join(CSRC, f) for f in ("dg_kernels.cuh", "dg_launch.cuh", "dg_batch.cuh", "dg_nvtx.h",
+                                             "gen_tables.py")] + \
         [os.path.join(INCLUDE, "dgswe.h")]
 
 

@@ -10,6 +10,7 @@
 
 #include "dg_batch.cuh"
 #include "dg_launch.cuh"
+#include "dg_nvtx.h"
 #include "dgswe.h"
 
 using namespace dgswe;
@@ -18,9 +19,15 @@ namespace {
 
 int K_of(int p) { return (p + 1) * (p + 2) / 2; }
 
+// Status of a failed CUDA call.  A failed allocation also leaves the
+// runtime's last-error slot set; it is cleared here, so that the next
+// launch check (cudaGetLastError) of a later call does not report it again.
 dg_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return DG_OK;
-  if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    return DG_ERR_OOM;
+  }
   return DG_ERR_CUDA;
 }
 
@@ -60,6 +67,8 @@ struct dg_batch {
   void* ghb = nullptr;
   void* lin = nullptr;          // FP64 batches only
   void* ahb = nullptr;          // mixed-solve batches only
+  double* stage = nullptr;      // FP64 staging for get/set state
+  size_t stage_n = 0;
   double* lam = nullptr;        // [2][n]
   double* t = nullptr;          // [n]
   unsigned* err = nullptr;
@@ -195,7 +204,7 @@ void free_batch(dg_batch* b) {
   if (!b) return;
   drop_graphs(b);
   void* bufs[] = {b->w[0], b->w[1], b->w[2], b->vs[0], b->vs[1], b->rec[0], b->rec[1], b->hb, b->hbt,
-                  b->ghb, b->lin, b->ahb, b->lam, b->t, b->err, b->counters, b->d_inst, b->d_items};
+                  b->ghb, b->lin, b->ahb, b->stage, b->lam, b->t, b->err, b->counters, b->d_inst, b->d_items};
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -205,10 +214,6 @@ void free_batch(dg_batch* b) {
 __global__ void cvt_f(const double* __restrict__ a, float* __restrict__ b, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = float(a[i]);
-}
-__global__ void cvt_b(const float* __restrict__ a, double* __restrict__ b, long long n) {
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = double(a[i]);
 }
 
 dg_status store_real(const dg_batch* b, const double* src, void* dst, long long n, cudaStream_t s) {
@@ -240,6 +245,7 @@ extern "C" {
 
 dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
                         const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out) {
+  dgswe::NvtxRange nvtx_range("dg_batch_init");
   if (n < 1 || !cfgs || !d_hb || !d_xi || !d_qx || !d_qy || !out) return DG_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     dg_status s = validate_one(&cfgs[i]);
@@ -396,6 +402,7 @@ dg_status dg_batch_set_block(dg_batch* b, int block) {
 }
 
 dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out) {
+  dgswe::NvtxRange nvtx_range("dg_batch_run");
   if (!b || nsteps < 0) return DG_ERR_ARG;
   if (!b->evaluated) {
     dg_status s = launch_eval(b, b->stream);
@@ -423,32 +430,60 @@ dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out) {
   return DG_OK;
 }
 
+// host FP64 staging of one instance's state [3][E][K] (grown on demand)
+static dg_status ensure_batch_stage(dg_batch* b, size_t doubles) {
+  if (b->stage_n >= doubles) return DG_OK;
+  if (b->stage) cudaFree(b->stage);
+  b->stage = nullptr;
+  b->stage_n = 0;
+  CK(cudaMalloc((void**)&b->stage, sizeof(double) * doubles));
+  b->stage_n = doubles;
+  return DG_OK;
+}
+
 dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy) {
+  dgswe::NvtxRange nvtx_range("dg_batch_get_state");
   if (!b || i < 0 || i >= b->n) return DG_ERR_ARG;
   const HostInst& h = b->inst[i];
   const long long E = h.E, KE = (long long)h.K * E;
-  std::vector<double> host((size_t)3 * KE);
-  double* tmp = nullptr;
-  CK(cudaMalloc(&tmp, sizeof(double) * 3 * KE));
+  dg_status s = ensure_batch_stage(b, (size_t)3 * KE);
+  if (s != DG_OK) return s;
+  // device transpose to element-major FP64, then one copy per field
   const char* src = (const char*)b->w[0] + h.o_state;
-  cudaError_t e = cudaSuccess;
-  if (b->arith == ARITH_FP64) {
-    e = cudaMemcpyAsync(tmp, src, sizeof(double) * 3 * KE, cudaMemcpyDeviceToDevice, b->stream);
-  } else {
-    cvt_b<<<(unsigned)((3 * KE + 255) / 256), 256, 0, b->stream>>>((const float*)src, tmp, 3 * KE);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(host.data(), tmp, sizeof(double) * 3 * KE, cudaMemcpyDeviceToHost, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-  cudaFree(tmp);
-  CK(e);
+  const unsigned g = (unsigned)((E + 127) / 128);
+  if (b->arith == ARITH_FP64)
+    soa_to_aos_kernel<double><<<g, 128, 0, b->stream>>>((const double*)src, b->stage, E, h.K, 3);
+  else
+    soa_to_aos_kernel<float><<<g, 128, 0, b->stream>>>((const float*)src, b->stage, E, h.K, 3);
+  CK(cudaGetLastError());
   double* dst[3] = {xi, qx, qy};
-  for (int f = 0; f < 3; ++f) {
-    if (!dst[f]) continue;
-    for (long long el = 0; el < E; ++el)
-      for (int k = 0; k < h.K; ++k) dst[f][(size_t)el * h.K + k] = host[(size_t)f * KE + (size_t)k * E + el];
-  }
+  for (int f = 0; f < 3; ++f)
+    if (dst[f])
+      CK(cudaMemcpyAsync(dst[f], b->stage + (size_t)f * KE, sizeof(double) * KE, cudaMemcpyDeviceToHost, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  return DG_OK;
+}
+
+dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double* qx, const double* qy, double t) {
+  dgswe::NvtxRange nvtx_range("dg_batch_set_state");
+  if (!b || i < 0 || i >= b->n || !xi || !qx || !qy) return DG_ERR_ARG;
+  const HostInst& h = b->inst[i];
+  const long long E = h.E, KE = (long long)h.K * E;
+  dg_status s = ensure_batch_stage(b, (size_t)3 * KE);
+  if (s != DG_OK) return s;
+  const double* src[3] = {xi, qx, qy};
+  for (int f = 0; f < 3; ++f)
+    CK(cudaMemcpyAsync(b->stage + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, b->stream));
+  char* dst = (char*)b->w[0] + h.o_state;
+  const unsigned g = (unsigned)((E + 127) / 128);
+  if (b->arith == ARITH_FP64)
+    aos_to_soa_kernel<double><<<g, 128, 0, b->stream>>>(b->stage, (double*)dst, E, h.K, 3);
+  else
+    aos_to_soa_kernel<float><<<g, 128, 0, b->stream>>>(b->stage, (float*)dst, E, h.K, 3);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(b->t + i, &t, sizeof(double), cudaMemcpyHostToDevice, b->stream));
+  CK(cudaStreamSynchronize(b->stream));
+  b->evaluated = false;   // the next run re-evaluates every instance
   return DG_OK;
 }
 
@@ -457,6 +492,7 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
 // and keeps the fastest.  ms_out[4] receives the time per step of 32, 64, 96
 // and 128.
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out) {
+  dgswe::NvtxRange nvtx_range("dg_batch_autotune");
   if (!b || trial_steps < 1) return DG_ERR_ARG;
   CK(cudaStreamSynchronize(b->stream));
   // snapshot of everything a step changes

@@ -125,6 +125,22 @@ cudaError_t static_fp32pir(int p, const Mesh& m, double g, const double* hb64, v
 // static FP64 bathymetry matrix of the mixed solve: ahb [K(K+1)/2][E]
 cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, double* ahb, cudaStream_t s);
 
+// FP64 element-major [F][E][K] <-> context-precision SoA [F][K][E] on the device
+template <class Real>
+__global__ void aos_to_soa_kernel(const double* __restrict__ a, Real* __restrict__ b, long long E, int K, int F) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  for (int f = 0; f < F; ++f)
+    for (int i = 0; i < K; ++i) b[((long long)f * K + i) * E + e] = Real(a[((long long)f * E + e) * K + i]);
+}
+template <class Real>
+__global__ void soa_to_aos_kernel(const Real* __restrict__ b, double* __restrict__ a, long long E, int K, int F) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  for (int f = 0; f < F; ++f)
+    for (int i = 0; i < K; ++i) a[((long long)f * E + e) * K + i] = double(b[((long long)f * K + i) * E + e]);
+}
+
 // fill the derived geometry of a uniform mesh
 inline Mesh make_mesh(int nx, int ny, double x0, double y0, double Lx, double Ly, bool periodic) {
   Mesh m;

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "dg_launch.cuh"
+#include "dg_nvtx.h"
 #include "dgswe.h"
 
 using namespace dgswe;
@@ -64,9 +65,15 @@ int K_of(int p) { return (p + 1) * (p + 2) / 2; }
 // basis size of the bathymetry space P^max(p,1)
 int KB_of(int p) { return K_of(p > 1 ? p : 1); }
 
+// Status of a failed CUDA call.  A failed allocation also leaves the
+// runtime's last-error slot set; it is cleared here, so that the next
+// launch check (cudaGetLastError) of a later call does not report it again.
 dg_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return DG_OK;
-  if (e == cudaErrorMemoryAllocation) return DG_ERR_OOM;
+  if (e == cudaErrorMemoryAllocation) {
+    (void)cudaGetLastError();
+    return DG_ERR_OOM;
+  }
   return DG_ERR_CUDA;
 }
 
@@ -272,21 +279,6 @@ __global__ void cvt_kernel_f(const double* __restrict__ a, float* __restrict__ b
   if (i < n) b[i] = float(a[i]);
 }
 
-// FP64 element-major [F][E][K] <-> context-precision SoA [F][K][E] on the device
-template <class Real>
-__global__ void aos_to_soa_kernel(const double* __restrict__ a, Real* __restrict__ b, long long E, int K, int F) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  for (int f = 0; f < F; ++f)
-    for (int i = 0; i < K; ++i) b[((long long)f * K + i) * E + e] = Real(a[((long long)f * E + e) * K + i]);
-}
-template <class Real>
-__global__ void soa_to_aos_kernel(const Real* __restrict__ b, double* __restrict__ a, long long E, int K, int F) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= E) return;
-  for (int f = 0; f < F; ++f)
-    for (int i = 0; i < K; ++i) a[((long long)f * E + e) * K + i] = double(b[((long long)f * K + i) * E + e]);
-}
 
 // device FP64 -> context precision
 dg_status store_real(const dg_ctx* c, const double* src, void* dst, long long n, cudaStream_t s) {
@@ -574,6 +566,7 @@ const char* dg_status_str(dg_status s) {
 
 dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_xi, const void* d_qx,
                          const void* d_qy, void* stream, dg_ctx** out) {
+  dgswe::NvtxRange nvtx_range("dg_init_device");
   dg_status s = validate(cfg);
   if (s != DG_OK) return s;
   if (!d_hb || !d_xi || !d_qx || !d_qy || !out) return DG_ERR_ARG;
@@ -583,6 +576,7 @@ dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_x
 
 dg_status dg_init(const dg_config* cfg, const double* hb, const double* xi, const double* qx, const double* qy,
                   void* stream, dg_ctx** out) {
+  dgswe::NvtxRange nvtx_range("dg_init");
   dg_status s = validate(cfg);
   if (s != DG_OK) return s;
   if (!hb || !xi || !qx || !qy || !out) return DG_ERR_ARG;
@@ -609,6 +603,7 @@ void dg_destroy(dg_ctx* ctx) {
 }
 
 dg_status dg_rhs(dg_ctx* c, const void* d_in, void* d_out) {
+  dgswe::NvtxRange nvtx_range("dg_rhs");
   if (!c || !d_in || !d_out || d_in == d_out) return DG_ERR_ARG;
   const long long E = c->E;
   if (!c->rhs_vs) {
@@ -640,6 +635,7 @@ dg_status dg_rhs(dg_ctx* c, const void* d_in, void* d_out) {
 }
 
 dg_status dg_run(dg_ctx* c, int nsteps, double* t_out) {
+  dgswe::NvtxRange nvtx_range("dg_run");
   if (!c || nsteps < 0) return DG_ERR_ARG;
   dg_status s = ensure_evaluated(c);
   if (s != DG_OK) return s;
@@ -658,6 +654,7 @@ dg_status dg_run(dg_ctx* c, int nsteps, double* t_out) {
 }
 
 dg_status dg_rk_step(dg_ctx* c, double* dt_used) {
+  dgswe::NvtxRange nvtx_range("dg_rk_step");
   if (!c) return DG_ERR_ARG;
   dg_status s = ensure_evaluated(c);
   if (s != DG_OK) return s;
@@ -680,12 +677,13 @@ dg_status dg_state_device(dg_ctx* c, void** d_state) {
 // first use, kept with the context): the caller's element-major arrays are
 // copied as they are (asynchronously; page-locked arrays copy fastest) and
 // transposed on the device.
-dg_status ensure_stage(dg_ctx* c) {
+static dg_status ensure_stage(dg_ctx* c) {
   if (!c->stage) CK(cudaMalloc((void**)&c->stage, sizeof(double) * 3 * (size_t)c->K * c->E));
   return DG_OK;
 }
 
 dg_status dg_get_state(dg_ctx* c, double* xi, double* qx, double* qy) {
+  dgswe::NvtxRange nvtx_range("dg_get_state");
   if (!c) return DG_ERR_ARG;
   dg_status s = ensure_stage(c);
   if (s != DG_OK) return s;
@@ -705,6 +703,7 @@ dg_status dg_get_state(dg_ctx* c, double* xi, double* qx, double* qy) {
 }
 
 dg_status dg_set_state(dg_ctx* c, const double* xi, const double* qx, const double* qy, double t) {
+  dgswe::NvtxRange nvtx_range("dg_set_state");
   if (!c || !xi || !qx || !qy) return DG_ERR_ARG;
   dg_status s = ensure_stage(c);
   if (s != DG_OK) return s;

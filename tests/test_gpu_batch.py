@@ -68,6 +68,29 @@ def test_batch_equals_single_contexts(precision, proj):
         B.dg_batch_destroy(b)
 
 
+def test_batch_set_state_resumes_bit_exactly():
+    """5 steps, every instance's state and time copied out and into a fresh
+    batch, 5 more steps: identical to 10 uninterrupted steps"""
+    inst = [_instance(k, *s, "fp32") for k, s in enumerate(SPECS)]
+    args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
+            [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
+    b1 = B.dg_batch_init(*args)
+    b2 = B.dg_batch_init(*args)
+    try:
+        t5 = B.dg_batch_run(b1, 5)
+        for i, (_, _, E, K) in enumerate(inst):
+            B.dg_batch_set_state(b2, i, *B.dg_batch_get_state(b1, i, E, K), t=float(t5[i]))
+        t1 = B.dg_batch_run(b1, 5)
+        t2 = B.dg_batch_run(b2, 5)
+        assert np.array_equal(t1, t2)
+        for i, (_, _, E, K) in enumerate(inst):
+            for a, r in zip(B.dg_batch_get_state(b2, i, E, K), B.dg_batch_get_state(b1, i, E, K)):
+                assert np.array_equal(a, r)
+    finally:
+        B.dg_batch_destroy(b1)
+        B.dg_batch_destroy(b2)
+
+
 def test_batch_autotune_keeps_state():
     inst = [_instance(k, *s, "fp32") for k, s in enumerate(SPECS)]
     args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],

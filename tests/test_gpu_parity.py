@@ -312,6 +312,68 @@ def test_dry_state_is_reported():
         B.dg_destroy(ctx)
 
 
+def test_nonfinite_state_is_reported():
+    """a NaN in the input discharge is reported as DG_ERR_NONFINITE"""
+    wl = I.hump_p1_32(n=8)
+    E, K = wl.E, wl.K
+    hb = np.zeros((E, K))
+    hb[:, 0] = 10.0 * np.sqrt(2.0)
+    z = np.zeros((E, K))
+    U = np.zeros((E, K))
+    U[7, 1] = np.nan
+    ctx = B.dg_init(_cfg(wl, dt=1e-4), hb, z, U, z)
+    try:
+        with pytest.raises(B.DGError) as ei:
+            B.dg_run(ctx, 1)
+        assert ei.value.status == B.DG_ERR_NONFINITE
+    finally:
+        B.dg_destroy(ctx)
+
+
+def test_device_allocation_failure_is_reported():
+    """a configuration whose buffers cannot fit is refused with DG_ERR_OOM
+    before any input is read (the host arrays are never touched)"""
+    import ctypes
+    cfg = B.make_config(30000, 30000, 4, bc="periodic", precision="fp64")   # ~1.8e9 triangles, p = 4
+    h = ctypes.c_void_p()
+    z = (ctypes.c_double * 1)()
+    assert B.load().dg_init(ctypes.byref(cfg), z, z, z, z, None, ctypes.byref(h)) == B.DG_ERR_OOM
+    torch.cuda.synchronize()
+    # the device stays usable
+    small = B.make_config(4, 4, 1)
+    E, K = B.dg_num_elements(small), 3
+    hb = np.zeros((E, K))
+    hb[:, 0] = 10.0
+    ctx = B.dg_init(small, hb, np.zeros((E, K)), np.zeros((E, K)), np.zeros((E, K)))
+    B.dg_destroy(ctx)
+
+
+def test_checkpoint_resume_through_file(oracle_mod, tmp_path):
+    """N steps, checkpoint to .npz, a new context resumes: bit-identical to 2N"""
+    from paper_1904_08684_gb300 import checkpoint
+    wl = I.waves_p2_512(n=10, p=2, ngauss=2)
+    o = oracle_mod.Oracle(wl.nx, wl.ny, 2, bc="periodic")
+    hb, xi, U, V = _state(o, wl)
+    for precision in ("fp64", "fp32"):
+        cfg = _cfg(wl, precision=precision)
+        ref = B.dg_init(cfg, hb, xi, U, V)
+        a = B.dg_init(cfg, hb, xi, U, V)
+        b = B.dg_init(cfg, hb, xi, U, V)
+        try:
+            t_ref = B.dg_run(ref, 20)
+            B.dg_run(a, 10)
+            path = str(tmp_path / ("ck_%s.npz" % precision))
+            checkpoint.save(path, a, cfg)
+            assert checkpoint.load(path, b, cfg) == B.dg_run(a, 0)
+            t_b = B.dg_run(b, 10)
+            assert t_b == t_ref
+            for x, y in zip(B.dg_get_state(b, o.E, o.K), B.dg_get_state(ref, o.E, o.K)):
+                assert np.array_equal(x, y)
+        finally:
+            for c in (ref, a, b):
+                B.dg_destroy(c)
+
+
 def test_rhs_friction_coriolis(oracle_mod):
     """bottom friction tau_bf and Coriolis f_c of Eq. (2) (source r of Eq. (5))"""
     wl = I.waves_p2_512(n=9, p=2, ngauss=2)
