@@ -472,7 +472,9 @@ def run_reference(args):
     wl = wls[0]
     sample = "oracle RHS (one RK stage) of 1/16 of the elements of %s, %d evaluations in %.1f s" % (
         ", ".join(w.name for w in wls), reps, el)
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    # n_gpus: the launch's N (the oracle itself runs on rank 0's host cores)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "device": "host CPU cores (FP64 oracle)",
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded SplitMix64 fields)",
