@@ -2,9 +2,11 @@
 benchmark times:
 
 * the large single instance: 2048 x 2048 quads (8,388,608 triangles), p = 4,
-  FP32 state with the FP64 velocity solve, periodic, 128-thread blocks;
+  FP32 state with the FP64 (or the mixed refined) velocity solve, periodic,
+  128-thread blocks;
 * the ensemble: all 256 instances of uneven size (64..384 quads a side) and
-  order (p = 1..3) in one batch, FP32 with the FP64 solve, autotuned block.
+  order (p = 1..3) in one batch, FP32 with the FP64 (or mixed) solve,
+  autotuned block.
 
 The oracle cannot evaluate these meshes whole, so it works on sampled
 elements and their domain of dependence: the seeded fields are projected by
@@ -75,7 +77,8 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def test_large_instance_p4_2048_rhs_sampled(oracle_mod):
+@pytest.mark.parametrize("proj", ["fp64", "mixed"])
+def test_large_instance_p4_2048_rhs_sampled(oracle_mod, proj):
     wl = I.waves_p4_2048()
     o = oracle_mod.Oracle(wl.nx, wl.ny, wl.p, bc="periodic", rk_order=3, cfl=wl.cfl)
     _, _, nb = o.geometry()
@@ -87,7 +90,8 @@ def test_large_instance_p4_2048_rhs_sampled(oracle_mod):
                                    U0=lambda x, y: 0.4 + 0.2 * np.sin(2 * np.pi * (x - y)),
                                    V0=lambda x, y: -0.25 + 0.1 * np.cos(4 * np.pi * x))
     ref = o.rhs(hb, xi, U, V, elems=S)[:, S, :]
-    cfg = B.make_config(wl.nx, wl.ny, wl.p, bc="periodic", precision="fp32", rk_order=3, cfl=wl.cfl)
+    cfg = B.make_config(wl.nx, wl.ny, wl.p, bc="periodic", precision="fp32", rk_order=3, cfl=wl.cfl,
+                        proj_precision=proj)
     ctx = B.dg_init(cfg, hb, xi, U, V)
     try:
         Si = torch.from_numpy(S.astype(np.int64)).cuda()
@@ -101,11 +105,12 @@ def test_large_instance_p4_2048_rhs_sampled(oracle_mod):
         B.dg_destroy(ctx)
     bar = 2e-5 * wl.nx / 13
     errs = [_rel(got[f], ref[f]) for f in range(3)]
-    print("p4-2048 FP32 RHS relative L2 per field:", errs)
+    print("p4-2048 FP32 (%s solve) RHS relative L2 per field:" % proj, errs)
     assert max(errs) <= bar, (errs, bar)
 
 
-def test_ensemble_batch_step_sampled(oracle_mod):
+@pytest.mark.parametrize("proj", ["fp64", "mixed"])
+def test_ensemble_batch_step_sampled(oracle_mod, proj):
     """one SSP-RK3 step of the whole 256-instance batch; three instances (one
     per order, the largest of each) checked against the oracle at samples"""
     wls = I.ensemble()
@@ -115,7 +120,8 @@ def test_ensemble_batch_step_sampled(oracle_mod):
         picks.append(max(cand, key=lambda k: wls[k].E))
     cfgs, fields, setups = [], [[], [], [], []], {}
     for k, wl in enumerate(wls):
-        cfg = B.make_config(wl.nx, wl.ny, wl.p, bc="periodic", precision="fp32", rk_order=3, cfl=wl.cfl)
+        cfg = B.make_config(wl.nx, wl.ny, wl.p, bc="periodic", precision="fp32", rk_order=3, cfl=wl.cfl,
+                            proj_precision=proj)
         cfgs.append(cfg)
         if k in picks:
             o = oracle_mod.Oracle(wl.nx, wl.ny, wl.p, bc="periodic", rk_order=3, cfl=wl.cfl)
@@ -164,8 +170,8 @@ def test_ensemble_batch_step_sampled(oracle_mod):
         w3 = (1.0 / 3.0) * w0[:, S0] + (2.0 / 3.0) * (w2[:, S0] + dt * R2[:, S0])
         got = np.stack(states[k])[:, S0]
         errs = [_rel(got[f], w3[f]) for f in range(3)]
-        print("ensemble instance %d (p = %d, %d x %d, block %d): relative L2 after one step %s"
-              % (k, wls[k].p, wls[k].nx, wls[k].ny, block, errs))
+        print("ensemble instance %d (p = %d, %d x %d, block %d, %s solve): relative L2 after one step %s"
+              % (k, wls[k].p, wls[k].nx, wls[k].ny, block, proj, errs))
         assert errs[0] <= 1e-5, (k, errs)
         bar = 2e-5 * max(wls[k].nx, wls[k].ny) / 13
         assert max(errs[1:]) <= bar, (k, errs, bar)
