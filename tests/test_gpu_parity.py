@@ -114,6 +114,28 @@ def test_rhs_fp32_state(oracle_mod, p, proj):
         assert _relL2(got[f], ref[f]) <= 2e-5, (f, _relL2(got[f], ref[f]))
 
 
+@pytest.mark.parametrize("block", [32, 64, 96])
+def test_rhs_block_sizes_and_state_pointer(oracle_mod, block):
+    """smaller thread blocks (more, ragged blocks) give the same RHS; the
+    context's own state (dg_state_device) serves as dg_rhs input"""
+    wl = I.waves_p2_512(n=13, p=2, ngauss=3)
+    wl.ny = 11
+    o = oracle_mod.Oracle(wl.nx, wl.ny, 2, bc="periodic")
+    hb, xi, U, V = _state(o, wl)
+    ref = o.rhs(hb, xi, U, V)
+    cfg = _cfg(wl, block_size=block)
+    got = _gpu_rhs(cfg, hb, xi, U, V)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+    ctx = B.dg_init(cfg, hb, xi, U, V)
+    try:
+        out = torch.empty((3, o.K, o.E), dtype=torch.float64, device="cuda")
+        B.dg_rhs(ctx, B.dg_state_device(ctx), out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().transpose(0, 2, 1), got)
+    finally:
+        B.dg_destroy(ctx)
+
+
 def test_rhs_nonsquare_domain(oracle_mod):
     """hx != hy exercises the diagonal normal and the adj(B) scaling."""
     wl = I.waves_p2_512(n=9, p=2, ngauss=2)

@@ -304,6 +304,43 @@ def test_lake_at_rest(oracle_mod, p, level, lin):
     assert np.abs(U1).max() <= 1e-12 and np.abs(V1).max() <= 1e-12
 
 
+@pytest.mark.parametrize("p", [0, 1, 2])
+def test_friction_coriolis_uniform_flow(oracle_mod, p):
+    """Eq. (2) sources on a uniform flow over flat bathymetry (periodic): all
+    fluxes are constant, so the RHS is exactly the source,
+    d_t (U, V) = -tau_bf (U, V) + f_c (V, -U), in the constant mode only;
+    and the time integration follows the closed-form solution
+    (U, V)(t) = e^{-tau t} R(-f t) (U0, V0) to the SSP-RK3 local error."""
+    # [0, 1000]^2 in 4 x 4 quads, dt = 0.5: the gravity-wave CFL number is
+    # ~0.2, so round-off modes of the uniform state stay bounded
+    tau, f, U0, V0, H0, dt = 0.005, 0.02, 0.7, -0.4, 10.0, 0.5
+    o = oracle_mod.Oracle(4, 4, p, bc="periodic", rk_order=3, dt=dt, tau_bf=tau, f_c=f, Lx=1000.0, Ly=1000.0)
+    hb = o.project_hb(lambda x, y: H0 + 0 * x)
+    xi = o.project(lambda x, y: 0 * x)
+    U = o.project(lambda x, y: U0 + 0 * x)
+    V = o.project(lambda x, y: V0 + 0 * x)
+    R = o.rhs(hb, xi, U, V)
+    c = np.sqrt(2.0)   # mean = sqrt(2) c_1
+    assert np.abs(R[0]).max() <= 1e-13
+    assert np.allclose(R[1][:, 0] * c, -tau * U0 + f * V0, rtol=0, atol=1e-13)
+    assert np.allclose(R[2][:, 0] * c, -tau * V0 - f * U0, rtol=0, atol=1e-13)
+    if o.K > 1:
+        assert np.abs(R[1:, :, 1:]).max() <= 1e-13
+    n = 200
+    _, U1, V1, t, _ = o.run(hb, xi, U, V, n)
+    assert abs(t - n * dt) <= 1e-12
+    decay = np.exp(-tau * t)
+    Ue = decay * (U0 * np.cos(f * t) + V0 * np.sin(f * t))
+    Ve = decay * (V0 * np.cos(f * t) - U0 * np.sin(f * t))
+    # SSP-RK3 is third order: global error ~ t (|lambda| dt)^3 / 24 with
+    # |lambda| = |tau + i f|
+    lam = np.hypot(tau, f)
+    bound = 2 * t * (lam * dt) ** 3 / 24 * np.hypot(U0, V0)
+    assert np.abs(U1[:, 0] * c - Ue).max() <= bound
+    assert np.abs(V1[:, 0] * c - Ve).max() <= bound
+    assert np.abs(U1[:, 0] * c - Ue).max() > 0      # the bound is not vacuous
+
+
 def test_mirror_symmetry(oracle_mod):
     """The mesh is invariant under (x, y) -> (y, x); a symmetric hump keeps
     xi(x, y) = xi(y, x) and U(x, y) = V(y, x)."""
