@@ -66,14 +66,14 @@ FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x 
 def _roofline(parts, precision, proj, launch_s, traffic):
     """Roofline of the stage kernel.  parts: [(p, E)] of the instances of one
     launch; launch_s: seconds per stage launch.  Algorithmic flops per
-    element and stage: 2 x the FMA counts of flops.SURVEY_FMA (velocity solve,
+    element and stage: 2 x the FMA counts of flops.ALGORITHMIC_FMA (velocity solve,
     rest).  FP64 path: all flops against the FP64 rate; FP32 state with FP64
     solve: the solve's flops against the FP64 rate (the pipe that binds),
     with the FP32 share beside it; FP32 state with a double-float or FP32
     solve: all flops against the FP32 rate."""
     from paper_1904_08684_gb300 import flops as FL
-    fsolve = sum(2 * FL.SURVEY_FMA[p][0] * E for p, E in parts)
-    frest = sum(2 * FL.SURVEY_FMA[p][1] * E for p, E in parts)
+    fsolve = sum(2 * FL.ALGORITHMIC_FMA[p][0] * E for p, E in parts)
+    frest = sum(2 * FL.ALGORITHMIC_FMA[p][1] * E for p, E in parts)
     word = 8 if precision == "fp64" else 4
     alg_bytes = sum(FL.stage_bytes(p, word) * E for p, E in parts)
     hbm_peak = _peaks().get("hbm_gbs")

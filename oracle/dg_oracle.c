@@ -20,8 +20,7 @@
  * orientation sign rule that the fast path uses, and it never assumes the
  * basis is orthonormal (mass matrices are assembled and Cholesky-factored).
  *
- * Readings of the paper where it is silent or garbled (listed in the design
- * notes as well):
+ * Readings of the paper where it is silent or garbled:
  *  - basis phi_ei = phi^_i o F_e^-1 (§2.2, below Eq. (14)); the mass matrix is
  *    then |det B_e| I for the printed orthonormal basis;
  *  - vertices of every triangle are counter-clockwise so det B_e > 0;

@@ -1237,16 +1237,28 @@ constexpr int stage_min_blocks() {
 
 template <int P, class Real, class PR, int MODE, int FEAT>
 __global__ void __launch_bounds__(128, (stage_min_blocks<P, Real>())) stage_kernel(const StageParams<Real> sp) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double lam_e = 0.0;
+  double lam_acc = 0.0;
   unsigned err = 0;
   double dt = 0.0;
   if constexpr (MODE == MODE_STAGE) {
     dt = sp.dt_fixed > 0.0 ? sp.dt_fixed : sp.cfl_num / sp.lam[0];
   }
-  if (e < sp.m.E) stage_element<P, Real, PR, MODE, FEAT>(sp, e, dt, lam_e, err);
+  if constexpr (std::is_same<Real, float>::value) {
+    // FP32 state: grid-stride over blocks of elements (the launch caps the
+    // grid at the resident CTAs)
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e - threadIdx.x < sp.m.E;
+         e += (long long)gridDim.x * blockDim.x) {
+      double lam_e = 0.0;
+      if (e < sp.m.E) stage_element<P, Real, PR, MODE, FEAT>(sp, e, dt, lam_e, err);
+      lam_acc = fmax(lam_acc, lam_e);
+    }
+  } else {
+    // FP64: one element per thread, the grid covers the mesh
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < sp.m.E) stage_element<P, Real, PR, MODE, FEAT>(sp, e, dt, lam_acc, err);
+  }
   if (sp.lam_next) {
-    const double l = block_max(lam_e);
+    const double l = block_max(lam_acc);
     if (threadIdx.x == 0) atomic_max_nonneg(sp.lam_next, l);
   }
   if (err) atomicOr(sp.err, err);

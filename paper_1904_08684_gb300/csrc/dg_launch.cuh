@@ -36,7 +36,20 @@ inline int arith_of(int precision, int proj_precision) {
 template <int P, class REAL, class PREAL, int FEAT, int MODE>
 cudaError_t launch_stage_pm(int block, const void* params, cudaStream_t s) {
   const StageParams<REAL>& sp = *static_cast<const StageParams<REAL>*>(params);
-  const long long g = (sp.m.E + block - 1) / block;
+  long long g = (sp.m.E + block - 1) / block;
+  if (std::is_same<REAL, float>::value) {
+    // FP32 state: a persistent grid of the resident CTAs (no partial last
+    // wave; measured 2-10 % faster).  FP64 keeps one CTA per element block
+    // (the capped grid measured 0.8 % slower there).
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<P, REAL, PREAL, MODE, FEAT>, block, 0);
+    if (e != cudaSuccess) return e;
+    const long long resident = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    if (g > resident) g = resident;
+  }
   stage_kernel<P, REAL, PREAL, MODE, FEAT><<<(unsigned)g, block, 0, s>>>(sp);
   return cudaGetLastError();
 }

@@ -37,12 +37,12 @@ def _tables(p):
 # of the velocity solve and FMAs of everything else, counted from the tensor
 # nonzeros (nnz T/2 + K^3/6 + 2K^2 for the solve; products, contractions,
 # traces, fluxes and lifts for the rest).
-SURVEY_FMA = {1: (28, 478), 2: (160, 1498), 3: (564, 4143), 4: (1588, 10344)}
+ALGORITHMIC_FMA = {1: (28, 478), 2: (160, 1498), 3: (564, 4143), 4: (1588, 10344)}
 
 
 def algorithmic_flops(p):
     """flops per element and stage (2 per FMA) of the reference count"""
-    a, b = SURVEY_FMA[p]
+    a, b = ALGORITHMIC_FMA[p]
     return 2 * (a + b)
 
 
