@@ -108,3 +108,37 @@ def test_full_size_rk3_step_sampled(full):
     for f in range(3):
         rel = np.linalg.norm(got[f] - w3[f]) / np.linalg.norm(w3[f])
         assert rel <= 1e-12, (f, rel)
+
+
+@pytest.mark.slow
+def test_coefficient_offsets_beyond_2_31():
+    """A mesh large enough that coefficient offsets (f K + i) E + e pass 2^31
+    (7800 x 7800 quads = 121.7 M triangles, p = 2, FP32; ~110 GB of device
+    state): a lake at rest over flat bathymetry has a zero RHS bit for bit and
+    stays at rest, so any 32-bit index wrap (which would read other buffers)
+    shows up as a non-zero value."""
+    n = 7800
+    cfg = B.make_config(n, n, 2, bc="periodic", precision="fp32", rk_order=3, cfl=0.2)
+    E, K = B.dg_num_elements(cfg), B.dg_num_basis(2)
+    assert 3 * K * E > 2 ** 31
+    hb = torch.zeros((B.dg_num_basis_bathymetry(2), E), dtype=torch.float64, device="cuda")
+    hb[0] = 10.0 / np.sqrt(2.0)           # depth 10 (phi_1 = sqrt(2))
+    z = torch.zeros((K, E), dtype=torch.float64, device="cuda")
+    ctx = B.dg_init_device(cfg, hb, z, z, z)
+    del hb, z
+    torch.cuda.empty_cache()
+    try:
+        out = torch.empty((3, K, E), dtype=torch.float32, device="cuda")
+        B.dg_rhs(ctx, B.dg_state_device(ctx), out)
+        torch.cuda.synchronize()
+        assert int(torch.count_nonzero(out)) == 0
+        t = B.dg_run(ctx, 2)
+        assert t > 0
+        B.dg_rhs(ctx, B.dg_state_device(ctx), out)
+        torch.cuda.synchronize()
+        assert int(torch.count_nonzero(out)) == 0
+        mass, energy = B.dg_diagnostics(ctx)
+        assert mass == 0.0 and energy == 0.0
+    finally:
+        B.dg_destroy(ctx)
+        torch.cuda.empty_cache()
