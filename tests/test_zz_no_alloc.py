@@ -29,21 +29,31 @@ def _fields(wl, seed):
               lambda x, y: 0.2 + 0.1 * torch.sin(2 * np.pi * (x + r[3])),
               lambda x, y: -0.1 + 0.05 * torch.cos(2 * np.pi * y)]
     out = []
-    for f in fields:
-        c = torch.empty((K, E), dtype=torch.float64, device="cuda")
-        B.dg_project(cfg, f(xy[0], xy[1]).contiguous(), c)
+    for k, f in enumerate(fields):
+        if k == 0 and wl.p == 0:
+            # h_b lives in P^max(p,1): project it with an order-1 rule
+            cfg1 = B.make_config(wl.nx, wl.ny, 1, bc=wl.bc)
+            xy1 = torch.empty((2, B.dg_proj_num_nodes(1), E), dtype=torch.float64, device="cuda")
+            B.dg_proj_nodes(cfg1, xy1)
+            c = torch.empty((B.dg_num_basis_bathymetry(0), E), dtype=torch.float64, device="cuda")
+            B.dg_project(cfg1, f(xy1[0], xy1[1]).contiguous(), c)
+        else:
+            c = torch.empty((K, E), dtype=torch.float64, device="cuda")
+            B.dg_project(cfg, f(xy[0], xy[1]).contiguous(), c)
         out.append(c)
     torch.cuda.synchronize()
     return out
 
 
-@pytest.mark.parametrize("precision,p", [("fp64", 2), ("fp64", 3), ("fp32", 3)])
-def test_noalloc_rhs_equals_dg_rhs_twice(precision, p):
+@pytest.mark.parametrize("precision,p,proj", [("fp64", 2, "fp64"), ("fp64", 3, "fp64"), ("fp32", 3, "fp64"),
+                                              ("fp64", 0, "fp64"), ("fp32", 3, "mixed"), ("fp32", 2, "df64")])
+def test_noalloc_rhs_equals_dg_rhs_twice(precision, p, proj):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     wl = I.waves_p2_512(n=37, p=p, ngauss=2)
     wl.ny = 29                                   # 2146 triangles, ragged last block
-    cfg = B.make_config(wl.nx, wl.ny, p, bc="periodic", precision=precision, rk_order=3, cfl=0.2)
+    cfg = B.make_config(wl.nx, wl.ny, p, bc="periodic", precision=precision, rk_order=3, cfl=0.2,
+                        proj_precision=proj)
     dt = torch.float64 if precision == "fp64" else torch.float32
     tol = 1e-13 if precision == "fp64" else 1e-5
     refs, inputs = [], []
