@@ -19,9 +19,10 @@
  *   v_ij+1), t = 1 upper triangle (v_i+1j+1, v_ij+1, v_i+1j), both
  *   counter-clockwise so det B_e > 0.
  * Basis (paper §2.2): on element e, phi_ei = phi^_i o F_e^-1 with the
- *   orthonormal reference functions printed in §2.2 (K = 3, 6, 10 for
- *   p = 1, 2, 3); p = 4 continues them by Gram-Schmidt of x^4, x^3 y,
- *   x^2 y^2, x y^3, y^4 (K = 15).  The mass matrix is |det B_e| I.
+ *   orthonormal reference functions printed in §2.2 (K = 1, 3, 6, 10 for
+ *   p = 0, 1, 2, 3); p = 4 continues them by Gram-Schmidt of x^4, x^3 y,
+ *   x^2 y^2, x y^3, y^4 (K = 15).  The mass matrix is |det B_e| I.  The
+ *   bathymetry h_b is a DG field of order max(p, 1).
  * Time stepping (not stated in the paper; §3.1 uses a fixed dt): SSP
  *   Runge-Kutta of order 1, 2 or 3 in Shu-Osher form; dt either fixed or
  *   cfl * d_min / ((2p+1) max_e (|u_e| + sqrt(g H_e))) with element means and
@@ -39,6 +40,8 @@
  *   - All device work is ordered on the stream given to dg_init (NULL = the
  *     legacy default stream).  Entry points that return host data
  *     synchronise that stream.
+ *   - A context or batch is used by one host thread at a time; distinct
+ *     contexts are independent of each other.
  *   - No C++ exception crosses this boundary; every failure is a dg_status.
  *     After DG_ERR_DRY or DG_ERR_NONFINITE the context stays valid so the
  *     state can be inspected; after DG_ERR_CUDA it should be destroyed.
