@@ -117,6 +117,7 @@ def test_coefficient_offsets_beyond_2_31():
     state): a lake at rest over flat bathymetry has a zero RHS bit for bit and
     stays at rest, so any 32-bit index wrap (which would read other buffers)
     shows up as a non-zero value."""
+    torch.cuda.empty_cache()            # return memory cached by earlier tests
     n = 7800
     cfg = B.make_config(n, n, 2, bc="periodic", precision="fp32", rk_order=3, cfl=0.2)
     E, K = B.dg_num_elements(cfg), B.dg_num_basis(2)
