@@ -48,3 +48,15 @@ def test_single_rank_passthrough():
     import bench
     ms, step_ms, value = bench.reduce_time_and_value(20.0, 500.0, 4, 1)
     assert (ms, step_ms) == (20.0, 5.0) and value == pytest.approx(500.0 * 1e3 / 5.0)
+
+
+@pytest.mark.parametrize("n,world", [(256, 2), (256, 8), (7, 4), (3, 4)])
+def test_ensemble_sharding_is_a_partition(n, world):
+    """every instance belongs to exactly one rank; rank loads differ by at
+    most one instance"""
+    import bench
+    parts = [bench.shard_instances(n, world, r) for r in range(world)]
+    flat = sorted(i for p in parts for i in p)
+    assert flat == list(range(n))
+    sizes = [len(p) for p in parts]
+    assert max(sizes) - min(sizes) <= 1
