@@ -105,3 +105,21 @@ def test_batch_rejects_mixed_or_unsupported_without_gpu(lib):
     with pytest.raises(B.DGError) as ei:
         B.dg_batch_init([], [], [], [], [])
     assert ei.value.status == B.DG_ERR_ARG
+
+
+def test_plain_c_program_uses_the_abi(lib, tmp_path):
+    """include/dgswe.h is valid C99 on its own, and a C program links the
+    library and gets the documented answers from the host-side calls"""
+    import shutil
+    import subprocess
+    from paper_1904_08684_gb300 import build as BLD
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    here = os.path.dirname(os.path.abspath(__file__))
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(BLD.LIB)
+    subprocess.check_call(["gcc", "-std=c99", "-Wall", "-Werror", "-I", BLD.INCLUDE,
+                           os.path.join(here, "c_abi_check.c"), "-L", libdir, "-ldgswe",
+                           "-Wl,-rpath," + libdir, "-o", exe])
+    res = subprocess.run([exe], capture_output=True, text=True)
+    assert res.returncode == 0 and res.stdout.strip() == "OK", (res.stdout, res.stderr)
