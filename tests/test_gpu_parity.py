@@ -114,6 +114,78 @@ def test_rhs_fp32_state(oracle_mod, p, proj):
         assert _relL2(got[f], ref[f]) <= 2e-5, (f, _relL2(got[f], ref[f]))
 
 
+def _weighted_mass_condition(o, H, e):
+    """condition number of A^H (Eq. (12)) on element e, assembled in FP64 from
+    the oracle's own L2 projection: column b = Pi(H phi_b)"""
+    xy = o.proj_nodes(np.array([e], dtype=np.int32))[0]
+    A = np.zeros((o.K, o.K))
+    for b in range(o.K):
+        c = np.zeros((o.E, o.K))
+        c[e, b] = 1.0
+        phib = np.array([o.eval_point(c, e, x, y) for x, y in xy])
+        col = np.zeros((o.E, o.K))
+        o.project_sub((H(xy[:, 0], xy[:, 1]) * phib)[None, :], [e], col)
+        A[:, b] = col[e]
+    w = np.linalg.eigvalsh(0.5 * (A + A.T))
+    return w[-1] / w[0]
+
+
+@pytest.mark.parametrize("p", [3, 4])
+def test_velocity_solve_ill_conditioned_element(oracle_mod, p):
+    """One element whose depth vanishes like lambda_1^p towards an edge
+    (H = 1e-3 + 10 lambda_1^p, a beach inside one triangle; depth 10
+    elsewhere): A^H of Eq. (12) then has kappa ~ 5e2 (p = 3) and ~ 3e3
+    (p = 4).  With the FP64, mixed (refined) and double-float solves the
+    momentum RHS of that element and its neighbours stays at the FP32 level
+    of the state (bar 2e-6 ~ 30 eps_32: sums of ~30 rounded products); the
+    FP32 solve adds an error ~ kappa eps_32, which at p = 4 is more than ten
+    times larger: the case the FP64 solve is there for."""
+    n, e0 = 8, 54
+    vx = np.array([[0.375, 0.375], [0.5, 0.375], [0.375, 0.5]])    # element 54, counter-clockwise
+
+    def lam1(x, y):
+        (x1, y1), (x2, y2), (x3, y3) = vx
+        det = (x2 - x1) * (y3 - y1) - (x3 - x1) * (y2 - y1)
+        l2 = ((x - x1) * (y3 - y1) - (x3 - x1) * (y - y1)) / det
+        l3 = ((x2 - x1) * (y - y1) - (x - x1) * (y2 - y1)) / det
+        return 1.0 - l2 - l3
+
+    def beach(x, y):
+        return 1e-3 + 10.0 * lam1(x, y) ** p
+
+    o = oracle_mod.Oracle(n, n, p, bc="reflective")
+    verts, _, nb = o.geometry()
+    assert np.allclose(np.sort(verts[e0], axis=0), np.sort(vx, axis=0))
+    kappa = _weighted_mass_condition(o, beach, e0)
+    assert kappa > (300 if p == 3 else 2000), kappa
+    hb = np.zeros((o.E, o.Kb))
+    hb[:, 0] = 10.0 / np.sqrt(2.0)          # phi_1 = sqrt(2): depth 10
+    xy = o.proj_nodes(np.array([e0], dtype=np.int32))
+    o.project_sub(beach(xy[..., 0], xy[..., 1]), [e0], hb, hb=True)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)    # noqa: E731
+    hb = f32(hb)
+    xi = np.zeros((o.E, o.K))
+    U = f32(o.project(lambda x, y: 0.3 + 0.1 * x))
+    V = f32(o.project(lambda x, y: -0.2 + 0.05 * y))
+    ref = o.rhs(hb, xi, U, V)
+    S = np.unique(np.concatenate([[e0], nb[e0][nb[e0] >= 0]]))
+    errs = {}
+    for proj in ("fp64", "mixed", "df64", "fp32"):
+        if proj == "df64" and p > 3:
+            continue
+        cfg = B.make_config(n, n, p, bc="reflective", precision="fp32", rk_order=3, cfl=0.2,
+                            proj_precision=proj)
+        got = _gpu_rhs(cfg, hb, xi, U, V, dtype=torch.float32)
+        errs[proj] = max(_relL2(got[f][S], ref[f][S]) for f in (1, 2))
+    print("p = %d, kappa(A^H) = %.0f: momentum RHS relative L2 near the element per solve %s"
+          % (p, kappa, {k: "%.2e" % v for k, v in errs.items()}))
+    for proj in ("fp64", "mixed", "df64"):
+        if proj in errs:
+            assert errs[proj] <= 2e-6, (proj, errs)
+    if p == 4:
+        assert errs["fp32"] >= 10 * errs["fp64"], errs
+
+
 @pytest.mark.parametrize("block", [32, 64, 96])
 def test_rhs_block_sizes_and_state_pointer(oracle_mod, block):
     """smaller thread blocks (more, ragged blocks) give the same RHS; the
@@ -226,6 +298,8 @@ def test_fp32_mixed_hump_p3_1000_steps(oracle_mod, proj):
         B.dg_destroy(ctx)
     assert abs(t - tr) <= 1e-5 * tr
     errs = [_relL2(g_, r_) for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr))]
+    print("hump-p3-32 FP32 state, %s solve, %d steps: relative L2 (xi, qx, qy) %s, mass drift %.2e"
+          % (proj, wl.steps, ["%.2e" % v for v in errs], (m1 - m0) / m0))
     # xi is measured around its mean state: the hump is the signal
     assert max(errs) <= 1e-5, errs
     assert abs(m1 - m0) <= 1e-5 * abs(m0)
