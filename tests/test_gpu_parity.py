@@ -387,9 +387,13 @@ def test_setup_projection_exact_on_polynomials(oracle_mod):
         assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
 
 
-def test_dry_state_is_reported():
+@pytest.mark.parametrize("precision,proj", [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "mixed"),
+                                             ("fp32", "df64"), ("fp32", "fp32")])
+def test_dry_state_is_reported(precision, proj):
     """A negative depth in the input is reported as DG_ERR_DRY, not a hang or
-    a fault, and the context stays usable."""
+    a fault, and the context stays usable; in every arithmetic (the mixed
+    solve's FP32 pivots fail there and it hands the element to the FP64
+    solve, which reports it)."""
     wl = I.hump_p1_32(n=8)
     E, K = wl.E, wl.K
     xi = np.zeros((E, K))
@@ -397,7 +401,7 @@ def test_dry_state_is_reported():
     hb[:, 0] = 10.0 * np.sqrt(2.0)
     hb[5, 0] = -3.0 * np.sqrt(2.0)      # one element with negative depth
     z = np.zeros((E, K))
-    ctx = B.dg_init(_cfg(wl, dt=1e-4), hb, xi, z, z)
+    ctx = B.dg_init(_cfg(wl, precision=precision, proj_precision=proj, dt=1e-4), hb, xi, z, z)
     try:
         with pytest.raises(B.DGError) as ei:
             B.dg_run(ctx, 1)
