@@ -454,7 +454,7 @@ def cpu_baseline(wl, seconds):
     repeated for about ``seconds``; one RHS evaluation is one RK stage."""
     sample = _oracle_sample(wl)
     dofs, el, reps = _time_sample(sample, seconds)
-    return {"value": dofs / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": dofs / el, "unit": UNIT, "cores": sample[0].threads(), "kind": "oracle",
             "sample": "oracle RHS (one RK stage) of elements 0..%d of %s, %d repetitions, %.1f s"
                       % (len(sample[4]) - 1, wl.name, reps, el)}
 
@@ -493,7 +493,7 @@ def run_reference(args):
            "data": "synthetic (seeded SplitMix64 fields)",
            "config": {"workload": args.workload, "elements": wl.E, "p": wl.p, "K": wl.K,
                       "rk_stages": wl.rk_order, "precision": "fp64", "bc": wl.bc},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[0][0].threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))

@@ -480,6 +480,8 @@ void or_destroy(void* hv) {
 }
 
 void or_set_threads(void* hv, int n) { ((or_ctx*)hv)->threads = n; }
+/* threads the element loops run on (the set count, else OpenMP's default) */
+int or_threads(void* hv) { return nthreads((or_ctx*)hv); }
 int or_num_elems(void* hv) { return ((or_ctx*)hv)->E; }
 int or_K(void* hv) { return ((or_ctx*)hv)->K; }
 int or_Kb(void* hv) { return ((or_ctx*)hv)->Kb; }

@@ -58,6 +58,7 @@ def _load():
         lib.or_create.argtypes = [ctypes.POINTER(_Cfg)]
         lib.or_destroy.argtypes = [vp]
         lib.or_set_threads.argtypes = [vp, ctypes.c_int]
+        lib.or_threads.argtypes = [vp]
         lib.or_num_elems.argtypes = [vp]
         lib.or_K.argtypes = [vp]
         lib.or_Kb.argtypes = [vp]
@@ -138,6 +139,10 @@ class Oracle:
 
     def set_threads(self, n):
         self.lib.or_set_threads(self._h, int(n))
+
+    def threads(self):
+        """threads the element loops run on"""
+        return int(self.lib.or_threads(self._h))
 
     # ---- geometry / basis -------------------------------------------------
     def basis_table(self):

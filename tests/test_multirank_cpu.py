@@ -60,3 +60,16 @@ def test_ensemble_sharding_is_a_partition(n, world):
     assert flat == list(range(n))
     sizes = [len(p) for p in parts]
     assert max(sizes) - min(sizes) <= 1
+
+
+def test_cpu_baseline_reports_the_threads_it_used(oracle_mod):
+    """the CPU baseline's core count is the oracle's thread count, not the
+    machine's"""
+    import bench
+    from paper_1904_08684_gb300 import inputs as I
+    sample = bench._oracle_sample(I.hump_p1_32(n=8))
+    sample[0].set_threads(1)
+    dofs, el, reps = bench._time_sample(sample, 0.05)
+    assert sample[0].threads() == 1 and reps >= 1 and dofs == 3 * 3 * len(sample[4]) * reps
+    sample[0].set_threads(0)
+    assert sample[0].threads() >= 1
