@@ -42,7 +42,8 @@
  *     synchronise that stream.
  *   - A context or batch is used by one host thread at a time; distinct
  *     contexts are independent of each other.
- *   - No C++ exception crosses this boundary; every failure is a dg_status.
+ *   - No C++ exception crosses this boundary; every failure is a dg_status
+ *     (a failed host allocation is DG_ERR_OOM, like a device one).
  *     After DG_ERR_DRY or DG_ERR_NONFINITE the context stays valid so the
  *     state can be inspected; after DG_ERR_CUDA it should be destroyed.
  */
@@ -59,7 +60,7 @@ typedef enum {
   DG_OK = 0,
   DG_ERR_ARG = 1,         /* invalid argument (null pointer, size, value)    */
   DG_ERR_UNSUPPORTED = 2, /* valid configuration this build does not provide */
-  DG_ERR_OOM = 3,         /* device allocation failed                        */
+  DG_ERR_OOM = 3,         /* device (or host) allocation failed              */
   DG_ERR_CUDA = 4,        /* a CUDA runtime call failed                      */
   DG_ERR_DRY = 5,         /* H <= 0 met: projection matrix not SPD or a
                              wave-speed point with non-positive depth      */
@@ -96,7 +97,8 @@ typedef struct {
                               perturbed meshes of §3.1); walls or Dirichlet
                               only, every triangle counter-clockwise; the
                               array is read by dg_init and not kept           */
-  int p;                   /* polynomial order, 1..4 (0 returns UNSUPPORTED)    */
+  int p;                   /* polynomial order, 0..4 (p = 0: the first-order
+                              finite-volume Lax-Friedrichs scheme)             */
   double g;                /* gravitational acceleration                        */
   int bc;                  /* dg_bc; DG_BC_DIRICHLET needs DG_FORCING_MANUFACTURED
                               (the only boundary data source)                 */
@@ -150,7 +152,9 @@ dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_x
  * Eq. (12)): d_rhs_out = M^-1 [ (A~, grad phi) - <A^, phi> + (r, phi) ] for
  * the state d_state_in.  Both device SoA [3][K][E] (fields xi, U, V) in the
  * context's precision; they must not overlap.  Uses the context's scratch
- * buffers; does not change the context's own state.  Asynchronous. */
+ * buffers (allocated on the first call); does not change the context's own
+ * state.  Asynchronous: a dry or non-finite input is not reported, and it
+ * does not touch the error state that dg_run reports. */
 dg_status dg_rhs(dg_ctx* ctx, const void* d_state_in, void* d_rhs_out);
 
 /* One SSP-RK step of the context's state.  If dt_used is not NULL the stream
@@ -191,7 +195,7 @@ dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, voi
  * CUDA graph is being captured, runtimes with a fixed device-memory budget
  * fixed at start-up, or hosts that forbid libraries from growing the device
  * heap -- and therefore cannot create a dg_ctx (dg_init allocates).
- *   cfg:        mesh, order, boundary, precision as for dg_init (p = 1..4,
+ *   cfg:        mesh, order, boundary, precision as for dg_init (p = 0..4,
  *               uniform mesh, periodic or reflective walls, no forcing);
  *               dt, cfl, rk_order are ignored.
  *   d_hb:       device FP64 SoA [Kb][E] bathymetry coefficients (input),
@@ -253,7 +257,8 @@ dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double*
  * return.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out);
 
-/* set the elements per work item (32, 64, 96 or 128; DG_ERR_ARG otherwise) */
+/* set the elements per work item (32, 64, 96 or 128; DG_ERR_ARG otherwise);
+ * on any error the batch keeps its previous setting */
 dg_status dg_batch_set_block(dg_batch* b, int block);
 
 /* degrees of freedom updated per RK stage: sum over instances of 3 K E */

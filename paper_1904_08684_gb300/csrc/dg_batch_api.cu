@@ -4,7 +4,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <climits>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <vector>
 
@@ -169,18 +171,21 @@ dg_status get_graph(dg_batch* b, cudaGraphExec_t* out) {
 // order's code at the same time; queues that mix orders (each class spread
 // evenly, so that FP64-bound and FP32-bound items overlap) measured 1.2-5x
 // slower, the warps stalling on instruction fetch.
+//
+// The batch changes only once the new list is on the device: on any failure
+// it keeps its previous items, block and graphs.
 dg_status build_items(dg_batch* b, int block) {
   std::vector<BatchItem> items;
-  for (int p = 3; p >= 1; --p)
-    for (int i = 0; i < b->n; ++i) {
-      if (b->inst[i].p != p) continue;
-      for (long long s = 0; s < b->inst[i].E; s += block) items.push_back({i, (int)s});
-    }
-  if (b->d_items) cudaFree(b->d_items);
-  b->d_items = nullptr;
-  CK(cudaMalloc(&b->d_items, sizeof(BatchItem) * items.size()));
-  CK(cudaMemcpy(b->d_items, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice));
-  b->n_items = (int)items.size();
+  try {
+    for (int p = 3; p >= 1; --p)
+      for (int i = 0; i < b->n; ++i) {
+        if (b->inst[i].p != p) continue;
+        for (long long s = 0; s < b->inst[i].E; s += block) items.push_back({i, (int)s});
+      }
+  } catch (const std::exception&) {   // no C++ exception crosses the C ABI
+    return DG_ERR_OOM;
+  }
+  if (items.size() > (size_t)INT_MAX) return DG_ERR_ARG;
   int occ = 0;
   cudaError_t e;
   switch (b->arith) {
@@ -194,9 +199,20 @@ dg_status build_items(dg_batch* b, int block) {
   int dev = 0, sms = 0;
   CK(cudaGetDevice(&dev));
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  BatchItem* d_new = nullptr;
+  CK(cudaMalloc(&d_new, sizeof(BatchItem) * items.size()));
+  const cudaError_t ce = cudaMemcpy(d_new, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
+  if (ce != cudaSuccess) {
+    cudaFree(d_new);
+    return cuda_status(ce);
+  }
+  // the captured graphs hold the old list's address: drop them with it
+  drop_graphs(b);
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = d_new;
+  b->n_items = (int)items.size();
   b->block = block;
   b->grid = std::max(1, std::min(b->n_items, sms * std::max(1, occ)));
-  drop_graphs(b);
   return DG_OK;
 }
 
@@ -257,6 +273,14 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   }
   dg_batch* b = new (std::nothrow) dg_batch();
   if (!b) return DG_ERR_OOM;
+  std::vector<BatchInst> desc;
+  try {
+    b->inst.reserve(n);
+    desc.resize(n);
+  } catch (const std::exception&) {   // no C++ exception crosses the C ABI
+    delete b;
+    return DG_ERR_OOM;
+  }
   b->n = n;
   b->arith = arith_of(cfgs[0].precision, cfgs[0].proj_precision);
   b->rsz = b->arith == ARITH_FP64 ? 8 : 4;
@@ -323,7 +347,6 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     return st;
   }
   cudaStream_t s = b->stream;
-  std::vector<BatchInst> desc(n);
   cudaError_t e = cudaMemsetAsync(b->lam, 0, sizeof(double) * 2 * n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->t, 0, sizeof(double) * n, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(b->err, 0, sizeof(unsigned), s);

@@ -150,6 +150,7 @@ extern "C" dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, cons
       cfg->precision > 1 || cfg->proj_precision < 0 || cfg->proj_precision > 3)
     return DG_ERR_ARG;
   if (cfg->bc == DG_BC_PERIODIC && (cfg->nx < 2 || cfg->ny < 2)) return DG_ERR_ARG;
+  if (!(cfg->tau_bf >= 0.0) || !std::isfinite(cfg->tau_bf) || !std::isfinite(cfg->f_c)) return DG_ERR_ARG;
   if (cfg->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
   if (cfg->precision == DG_PREC_FP32_MIXED && cfg->proj_precision == DG_PROJ_DF64 && cfg->p > 3)
     return DG_ERR_UNSUPPORTED;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <exception>
 #include <vector>
 
 #include "dg_kernels.cuh"
@@ -174,7 +175,12 @@ dg_status dg_proj_nodes(const dg_config* cfg, void* d_xy, void* stream) {
   // general mesh: element maps from the vertices (set-up only)
   const int nx = cfg->nx, ny = cfg->ny;
   const long long E = g.E;
-  std::vector<double> map((size_t)6 * E);
+  std::vector<double> map;
+  try {
+    map.resize((size_t)6 * E);
+  } catch (const std::exception&) {   // no C++ exception crosses the C ABI
+    return DG_ERR_OOM;
+  }
   const double* v = cfg->vertex_xy;
   auto vx = [&](int i, int j) { return v[2 * ((size_t)j * (nx + 1) + i)]; };
   auto vy = [&](int i, int j) { return v[2 * ((size_t)j * (nx + 1) + i) + 1]; };
@@ -193,7 +199,10 @@ dg_status dg_proj_nodes(const dg_config* cfg, void* d_xy, void* stream) {
         map[5 * E + e] = vy(i3, j3) - vy(i1, j1);
       }
   double* d = nullptr;
-  if (cudaMalloc(&d, sizeof(double) * map.size()) != cudaSuccess) return DG_ERR_OOM;
+  if (cudaMalloc(&d, sizeof(double) * map.size()) != cudaSuccess) {
+    (void)cudaGetLastError();   // clear the failed allocation from the last-error slot
+    return DG_ERR_OOM;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemcpyAsync(d, map.data(), sizeof(double) * map.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) {

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <exception>
 #include <new>
 #include <vector>
 
@@ -53,6 +54,7 @@ struct dg_ctx {
   double* stage;         // FP64 AoS staging buffer [3][E][K] for host copies
   void* rhs_vs;          // scratch of dg_rhs
   void* rhs_rec;
+  unsigned* rhs_err;     // error word of dg_rhs (kept apart from the time loop's)
   int ep;                // eval buffer holding the current state's evaluation
   int lc;                // wave-speed slot of the current state
   bool evaluated;
@@ -266,7 +268,12 @@ dg_status read_err(dg_ctx* c) {
 // host AoS FP64 [E][K] -> device SoA FP64 [K][E] (staging through a pinned
 // or pageable host transpose)
 dg_status upload_soa(const double* host, long long E, int K, double* dev, cudaStream_t s) {
-  std::vector<double> t((size_t)E * K);
+  std::vector<double> t;
+  try {
+    t.resize((size_t)E * K);
+  } catch (const std::exception&) {   // no C++ exception crosses the C ABI
+    return DG_ERR_OOM;
+  }
   for (long long e = 0; e < E; ++e)
     for (int i = 0; i < K; ++i) t[(size_t)i * E + e] = host[(size_t)e * K + i];
   CK(cudaMemcpyAsync(dev, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, s));
@@ -297,7 +304,7 @@ void free_ctx(dg_ctx* c) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
   void* bufs[] = {c->w[0], c->w[1], c->w[2], c->vs[0], c->vs[1], c->rec[0], c->rec[1], c->hb, c->hbt,
                   c->ghb, c->lin, c->ahb, c->geo, c->vq, c->eq, c->scal, c->err, c->partial, c->rhs_vs, c->rhs_rec,
-                  c->stage};
+                  c->rhs_err, c->stage};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -448,7 +455,12 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   double dmin = 4.0 * (0.5 * c->det) / (hx + hy + std::hypot(hx, hy));
   std::vector<double> geo_h;
   if (cfg->vertex_xy) {
-    dg_status gs = build_geometry(cfg, geo_h, &dmin);
+    dg_status gs;
+    try {
+      gs = build_geometry(cfg, geo_h, &dmin);
+    } catch (const std::exception&) {
+      gs = DG_ERR_OOM;
+    }
     if (gs != DG_OK) {
       delete c;
       return gs;
@@ -477,7 +489,12 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   if (!geo_h.empty()) alloc((void**)&c->geo, sizeof(double) * geo_h.size());
   std::vector<double> vq_h, eq_h;
   if (cfg->forcing == DG_FORCING_MANUFACTURED) {
-    build_rules(cfg->p, vq_h, eq_h, &c->nqv, &c->nqe);
+    try {
+      build_rules(cfg->p, vq_h, eq_h, &c->nqv, &c->nqe);
+    } catch (const std::exception&) {
+      free_ctx(c);
+      return DG_ERR_OOM;
+    }
     alloc((void**)&c->vq, sizeof(double) * vq_h.size());
     alloc((void**)&c->eq, sizeof(double) * eq_h.size());
   }
@@ -606,12 +623,13 @@ dg_status dg_rhs(dg_ctx* c, const void* d_in, void* d_out) {
   dgswe::NvtxRange nvtx_range("dg_rhs");
   if (!c || !d_in || !d_out || d_in == d_out) return DG_ERR_ARG;
   const long long E = c->E;
-  if (!c->rhs_vs) {
-    CK(cudaMalloc(&c->rhs_vs, (size_t)3 * c->K * E * c->rsz));
-    CK(cudaMalloc(&c->rhs_rec, (size_t)3 * c->NREC * E * c->rsz));
-  }
+  // each buffer on its own: a failed allocation leaves the others for a retry
+  if (!c->rhs_vs) CK(cudaMalloc(&c->rhs_vs, (size_t)3 * c->K * E * c->rsz));
+  if (!c->rhs_rec) CK(cudaMalloc(&c->rhs_rec, (size_t)3 * c->NREC * E * c->rsz));
+  if (!c->rhs_err) CK(cudaMalloc((void**)&c->rhs_err, sizeof(unsigned)));
   if (c->arith == ARITH_FP64) {
     StageParams<double> sp = base_params<double>(c);
+    sp.err = c->rhs_err;
     sp.w = (const double*)d_in;
     sp.vs_out = (double*)c->rhs_vs;
     sp.rec_out = (double*)c->rhs_rec;
@@ -622,6 +640,7 @@ dg_status dg_rhs(dg_ctx* c, const void* d_in, void* d_out) {
     CK(launch_stage_any(c, MODE_RHS, &sp, c->stream));
   } else {
     StageParams<float> sp = base_params<float>(c);
+    sp.err = c->rhs_err;
     sp.w = (const float*)d_in;
     sp.vs_out = (float*)c->rhs_vs;
     sp.rec_out = (float*)c->rhs_rec;
@@ -741,7 +760,13 @@ dg_status dg_diagnostics(dg_ctx* c, double* mass, double* energy) {
     default: e = diag_fp32p32(c->P, c->mesh, c->w[0], c->hb, c->det, c->cfg.g, c->partial, c->stream); break;
   }
   CK(e);
-  std::vector<double> h((size_t)2 * nb);
+  std::vector<double> h;
+  try {
+    h.resize((size_t)2 * nb);
+  } catch (const std::exception&) {
+    (void)cudaStreamSynchronize(c->stream);
+    return DG_ERR_OOM;
+  }
   CK(cudaMemcpyAsync(h.data(), c->partial, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   double m = 0.0, en = 0.0;

@@ -46,13 +46,18 @@ def algorithmic_flops(p):
     return 2 * (a + b)
 
 
+# the files that define the stage and batch kernels' device code, their
+# reference tables and their launch shapes (host-only API code excluded)
+KERNEL_SOURCES = ("dg_aux_inst.cu", "dg_batch.cuh", "dg_batch_inst.cu", "dg_dispatch.cu", "dg_kernels.cuh",
+                  "dg_launch.cuh", "dg_stage_inst.cu", "gen_tables.py")
+
+
 def source_hash():
     """hash of the kernel sources: measured traffic is valid only for it"""
     h = hashlib.sha1()
-    for name in sorted(os.listdir(_CSRC)):
-        if name.endswith((".cu", ".cuh", ".py")):
-            with open(os.path.join(_CSRC, name), "rb") as f:
-                h.update(name.encode() + f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(_CSRC, name), "rb") as f:
+            h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
 
 

@@ -412,6 +412,38 @@ def test_dry_state_is_reported(precision, proj):
         B.dg_destroy(ctx)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_rhs_of_a_dry_trial_state_leaves_the_time_loop_clean(precision):
+    """dg_rhs of some other (here dry) state has its own error word: the
+    context's next dg_run, on its own healthy state, reports DG_OK, and the
+    state it reaches equals a context that never saw the dry right-hand side"""
+    wl = I.hump_p1_32(n=8)
+    E, K = wl.E, wl.K
+    hb = np.zeros((E, K))
+    hb[:, 0] = 10.0 * np.sqrt(2.0)
+    xi = np.zeros((E, K))
+    xi[:, 0] = 0.01 * np.sin(np.arange(E))
+    z = np.zeros((E, K))
+    dry = xi.copy()
+    dry[5, 0] = -12.0 * np.sqrt(2.0)      # H < 0 on element 5
+    dtype = torch.float64 if precision == "fp64" else torch.float32
+    cfg = _cfg(wl, precision=precision, dt=1e-4)
+    ctx = B.dg_init(cfg, hb, xi, z, z)
+    ref = B.dg_init(cfg, hb, xi, z, z)
+    try:
+        st = _to_soa([dry, z, z], dtype)
+        out = torch.empty_like(st)
+        B.dg_rhs(ctx, st, out)
+        torch.cuda.synchronize()
+        B.dg_run(ctx, 2)                      # raises on a reported error
+        B.dg_run(ref, 2)
+        for a, b in zip(B.dg_get_state(ctx, E, K), B.dg_get_state(ref, E, K)):
+            assert np.array_equal(a, b)
+    finally:
+        B.dg_destroy(ctx)
+        B.dg_destroy(ref)
+
+
 def test_nonfinite_state_is_reported():
     """a NaN in the input discharge is reported as DG_ERR_NONFINITE"""
     wl = I.hump_p1_32(n=8)
