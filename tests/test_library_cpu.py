@@ -123,3 +123,58 @@ def test_plain_c_program_uses_the_abi(lib, tmp_path):
                            "-Wl,-rpath," + libdir, "-o", exe])
     res = subprocess.run([exe], capture_output=True, text=True)
     assert res.returncode == 0 and res.stdout.strip() == "OK", (res.stdout, res.stderr)
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(tau_bf=-1.0), "ARG"), (dict(tau_bf=float("nan")), "ARG"), (dict(f_c=float("inf")), "ARG"),
+    (dict(p=5), "ARG"), (dict(bc="dirichlet"), "ARG"), (dict(nx=1, ny=1, bc="periodic"), "ARG"),
+    (dict(block_size=48), "ARG"), (dict(forcing=1), "UNSUPPORTED"),
+    (dict(precision="fp32", proj_precision="df64", p=4), "UNSUPPORTED"),
+    (dict(nx=8000, ny=8000), "ARG"),            # beyond the entry point's mesh limit
+    (dict(nx=200, ny=200, p=2), "ARG"),         # 80,000 FP64 triangles: beyond the fixed array
+])
+def test_noalloc_rhs_rejects_before_any_gpu_work(lib, bad, status):
+    """the allocation-free RHS validates its configuration and checks that
+    the mesh fits its fixed array before any CUDA call (so on a CPU host)"""
+    from paper_1904_08684_gb300 import binding as B
+    kw = dict(nx=4, ny=4, p=1, bc="periodic")
+    kw.update(bad)
+    cfg = B.make_config(**kw)
+    fake = [ctypes.c_void_p(0x1000 * (k + 1)) for k in range(3)]   # never dereferenced
+    got = B.load().dg_rhs_noalloc(ctypes.byref(cfg), fake[0], fake[1], fake[2], None)
+    assert got == getattr(B, "DG_ERR_" + status)
+    # the same pointer as input and output is refused
+    ok_cfg = B.make_config(4, 4, 1)
+    assert B.load().dg_rhs_noalloc(ctypes.byref(ok_cfg), fake[0], fake[1], fake[1], None) == B.DG_ERR_ARG
+
+
+def test_null_handles_are_rejected(lib):
+    """every entry point taking a context or batch refuses NULL on the host"""
+    from paper_1904_08684_gb300 import binding as B
+    L = B.load()
+    d = ctypes.c_double()
+    p = ctypes.c_void_p(0x1000)
+    assert L.dg_rhs(None, p, ctypes.c_void_p(0x2000)) == B.DG_ERR_ARG
+    assert L.dg_run(None, 1, ctypes.byref(d)) == B.DG_ERR_ARG
+    assert L.dg_rk_step(None, ctypes.byref(d)) == B.DG_ERR_ARG
+    assert L.dg_get_state(None, None, None, None) == B.DG_ERR_ARG
+    assert L.dg_set_state(None, None, None, None, 0.0) == B.DG_ERR_ARG
+    assert L.dg_diagnostics(None, ctypes.byref(d), ctypes.byref(d)) == B.DG_ERR_ARG
+    assert L.dg_state_device(None, ctypes.byref(ctypes.c_void_p())) == B.DG_ERR_ARG
+    assert L.dg_batch_run(None, 1, None) == B.DG_ERR_ARG
+    assert L.dg_batch_set_block(None, 64) == B.DG_ERR_ARG
+    assert L.dg_batch_get_state(None, 0, None, None, None) == B.DG_ERR_ARG
+    assert L.dg_batch_set_state(None, 0, None, None, None, 0.0) == B.DG_ERR_ARG
+    assert L.dg_batch_autotune(None, 1, None, None) == B.DG_ERR_ARG
+    assert L.dg_batch_dofs(None) == 0
+    L.dg_destroy(None)
+    L.dg_batch_destroy(None)
+
+
+def test_friction_must_be_a_finite_nonnegative_number(lib):
+    from paper_1904_08684_gb300 import binding as B
+    z = (ctypes.c_double * 1)()
+    h = ctypes.c_void_p()
+    for kw in (dict(tau_bf=-0.1), dict(tau_bf=float("nan")), dict(f_c=float("nan"))):
+        cfg = B.make_config(4, 4, 1, **kw)
+        assert B.load().dg_init(ctypes.byref(cfg), z, z, z, z, None, ctypes.byref(h)) == B.DG_ERR_ARG
