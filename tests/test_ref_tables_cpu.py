@@ -131,3 +131,19 @@ def test_edge_restriction_and_edge_products(tables, basis, p):
     # recovered from its Legendre coefficients when its trace has degree <= p
     for (gx, gy), Re in zip(gamma, tables[p]["R"]):
         assert np.abs(Re.T @ L - _eval(basis[:K], gx, gy)).max() <= 50 * TOL[p]
+
+
+def test_roofline_counts_follow_the_tables(tables):
+    """bench.py's algorithmic FMA counts: the velocity solve is
+    nnz(T)/2 (assembly of A^H) + K^3/6 (LDL^T) + 2K^2 (two solves), and the
+    rest covers at least the five projected products (5 nnz T) and the
+    volume contraction (3 nnz S)"""
+    from paper_1904_08684_gb300 import flops as FL
+    for p in (1, 2, 3, 4):
+        K = _K(p)
+        nnzT = int(np.count_nonzero(tables[p]["T"]))
+        nnzS = int(np.count_nonzero(tables[p]["S"]))
+        solve, rest = FL.ALGORITHMIC_FMA[p]
+        assert solve == round(nnzT / 2 + K ** 3 / 6 + 2 * K * K)
+        assert rest >= 5 * nnzT + 3 * nnzS
+        assert FL.algorithmic_flops(p) == 2 * (solve + rest)
