@@ -47,46 +47,69 @@ class _Cfg(ctypes.Structure):
 _lib = None
 
 
+def build_variant(src_text, tag, outdir):
+    """Compile a modified copy of the oracle source into ``outdir`` and load
+    it: tests plant a deliberate mistake in the oracle this way (on the CPU)
+    to check that a pin catches it.  Returns a library handle for
+    ``Oracle(..., lib=...)``."""
+    os.makedirs(outdir, exist_ok=True)
+    src = os.path.join(outdir, "dg_oracle_%s.c" % tag)
+    so = os.path.join(outdir, "libdgoracle_%s.so" % tag)
+    with open(src, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-std=c11", "-shared", "-fPIC", "-o", so, src, "-lm"])
+    return _configure(ctypes.CDLL(so))
+
+
+def source():
+    """text of the oracle's C source"""
+    with open(_SRC) as f:
+        return f.read()
+
+
 def _load():
     global _lib
     if _lib is None:
-        lib = ctypes.CDLL(build_oracle())
-        dp = ctypes.POINTER(ctypes.c_double)
-        ip = ctypes.POINTER(ctypes.c_int)
-        vp = ctypes.c_void_p
-        lib.or_create.restype = vp
-        lib.or_create.argtypes = [ctypes.POINTER(_Cfg)]
-        lib.or_destroy.argtypes = [vp]
-        lib.or_set_threads.argtypes = [vp, ctypes.c_int]
-        lib.or_threads.argtypes = [vp]
-        lib.or_num_elems.argtypes = [vp]
-        lib.or_K.argtypes = [vp]
-        lib.or_Kb.argtypes = [vp]
-        lib.or_project_hb.argtypes = [vp, dp, dp]
-        lib.or_dmin.argtypes = [vp]
-        lib.or_dmin.restype = ctypes.c_double
-        lib.or_basis_table.argtypes = [vp, dp]
-        lib.or_geometry.argtypes = [vp, dp, dp, ip]
-        lib.or_eval_point.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
-        lib.or_eval_point.restype = ctypes.c_double
-        lib.or_num_proj_nodes.argtypes = [vp]
-        lib.or_proj_nodes.argtypes = [vp, dp]
-        lib.or_proj_nodes_sub.argtypes = [vp, ip, ctypes.c_int, dp]
-        lib.or_project.argtypes = [vp, dp, dp]
-        lib.or_project_sub.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int, dp, dp]
-        lib.or_project_u.argtypes = [vp, dp, dp, dp, dp, dp, dp]
-        lib.or_rhs.argtypes = [vp, dp, dp, dp, dp, ctypes.c_double, ip, ctypes.c_int, dp, dp, dp]
-        lib.or_max_wave_speed.argtypes = [vp, dp, dp, dp, dp]
-        lib.or_max_wave_speed.restype = ctypes.c_double
-        lib.or_cfl_dt.argtypes = [vp, dp, dp, dp, dp]
-        lib.or_cfl_dt.restype = ctypes.c_double
-        lib.or_run.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, dp, dp]
-        lib.or_diagnostics.argtypes = [vp, dp, dp, dp, dp, dp, dp]
-        lib.or_ms_errors.argtypes = [vp, dp, dp, dp, ctypes.c_double, dp]
-        lib.or_ms_point.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                    ctypes.c_double, dp]
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build_oracle()))
     return _lib
+
+
+def _configure(lib):
+    dp = ctypes.POINTER(ctypes.c_double)
+    ip = ctypes.POINTER(ctypes.c_int)
+    vp = ctypes.c_void_p
+    lib.or_create.restype = vp
+    lib.or_create.argtypes = [ctypes.POINTER(_Cfg)]
+    lib.or_destroy.argtypes = [vp]
+    lib.or_set_threads.argtypes = [vp, ctypes.c_int]
+    lib.or_threads.argtypes = [vp]
+    lib.or_num_elems.argtypes = [vp]
+    lib.or_K.argtypes = [vp]
+    lib.or_Kb.argtypes = [vp]
+    lib.or_project_hb.argtypes = [vp, dp, dp]
+    lib.or_dmin.argtypes = [vp]
+    lib.or_dmin.restype = ctypes.c_double
+    lib.or_basis_table.argtypes = [vp, dp]
+    lib.or_geometry.argtypes = [vp, dp, dp, ip]
+    lib.or_eval_point.argtypes = [vp, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lib.or_eval_point.restype = ctypes.c_double
+    lib.or_num_proj_nodes.argtypes = [vp]
+    lib.or_proj_nodes.argtypes = [vp, dp]
+    lib.or_proj_nodes_sub.argtypes = [vp, ip, ctypes.c_int, dp]
+    lib.or_project.argtypes = [vp, dp, dp]
+    lib.or_project_sub.argtypes = [vp, ctypes.c_int, ip, ctypes.c_int, dp, dp]
+    lib.or_project_u.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+    lib.or_rhs.argtypes = [vp, dp, dp, dp, dp, ctypes.c_double, ip, ctypes.c_int, dp, dp, dp]
+    lib.or_max_wave_speed.argtypes = [vp, dp, dp, dp, dp]
+    lib.or_max_wave_speed.restype = ctypes.c_double
+    lib.or_cfl_dt.argtypes = [vp, dp, dp, dp, dp]
+    lib.or_cfl_dt.restype = ctypes.c_double
+    lib.or_run.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int, dp, dp]
+    lib.or_diagnostics.argtypes = [vp, dp, dp, dp, dp, dp, dp]
+    lib.or_ms_errors.argtypes = [vp, dp, dp, dp, ctypes.c_double, dp]
+    lib.or_ms_point.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.c_double, dp]
+    return lib
 
 
 def _ptr(a):
@@ -112,8 +135,8 @@ class Oracle:
 
     def __init__(self, nx, ny, p, bc="periodic", x0=0.0, y0=0.0, Lx=1.0, Ly=1.0, g=9.81,
                  rk_order=3, cfl=0.2, dt=0.0, vertex_xy=None, tau_bf=0.0, f_c=0.0,
-                 manufactured=False, threads=0, quad_extra=0):
-        lib = _load()
+                 manufactured=False, threads=0, quad_extra=0, lib=None):
+        lib = lib if lib is not None else _load()
         self._vxy = None if vertex_xy is None else _f64(vertex_xy).ravel()
         cfg = _Cfg(nx, ny, x0, y0, Lx, Ly,
                    None if self._vxy is None else _ptr(self._vxy),

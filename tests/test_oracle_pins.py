@@ -442,3 +442,237 @@ def test_table1_error_magnitude(oracle_mod, p):
     err = _manufactured_run(oracle_mod, 2, p, 1500.0)
     ratio = err / row[2:5]
     assert (ratio > 0.25).all() and (ratio < 4.0).all(), (err, row[2:5])
+
+
+# ---------------------------------------------------------------- LF wave speed
+# Reading of the Lax-Friedrichs flux named after Eq. (12) (§2.2): one wave
+# speed per edge, lambda = max over both sides and the edge points
+# s = 0, 1/2, 1 of |u.n| + sqrt(g H).  The pin below evaluates one edge's
+# flux integral independently (numpy, the printed degree-1 basis through its
+# vertex values, the mesh's documented vertex layout) and compares the
+# change it causes in the neighbouring element's RHS with the oracle's.
+
+_LAM_N, _LAM_L, _LAM_G = 4, 1.0, 9.81
+
+
+def _p1_vertex_matrix():
+    """Phi[k, i] = phi^_i at reference vertex k ((0,0), (1,0), (0,1)),
+    printed degree-1 functions of §2.2"""
+    ref = _golden("basis_vertex_values.txt")
+    return ref[:3, 1:].T
+
+
+def _lower_triangle(i, j, n=_LAM_N, L=_LAM_L):
+    """vertices (v_ij, v_i+1j, v_ij+1) of the lower triangle of quad (i, j)"""
+    h = L / n
+    return np.array([[i * h, j * h], [(i + 1) * h, j * h], [i * h, (j + 1) * h]])
+
+
+def _upper_triangle(i, j, n=_LAM_N, L=_LAM_L):
+    """vertices (v_i+1j+1, v_ij+1, v_i+1j) of the upper triangle of quad (i, j)"""
+    h = L / n
+    return np.array([[(i + 1) * h, (j + 1) * h], [i * h, (j + 1) * h], [(i + 1) * h, j * h]])
+
+
+def _p1_coefficients(f, verts):
+    """coefficients of the linear function f in the basis phi^_i o F_e^-1:
+    sum_i c_i phi^_i(vertex k) = f(vertex k)"""
+    vals = np.array([f(x, y) for x, y in verts])
+    return np.linalg.solve(_p1_vertex_matrix(), vals)
+
+
+def _p1_basis_at(verts, x, y):
+    """phi_ei(x, y) by barycentric interpolation of the vertex values"""
+    T = np.array([[verts[1, 0] - verts[0, 0], verts[2, 0] - verts[0, 0]],
+                  [verts[1, 1] - verts[0, 1], verts[2, 1] - verts[0, 1]]])
+    xr, yr = np.linalg.solve(T, np.array([x, y]) - verts[0])
+    bary = np.array([1.0 - xr - yr, xr, yr])
+    return bary @ _p1_vertex_matrix()
+
+
+def _lam_case():
+    """Flat bathymetry and constant elevation (so H is constant and u = q/H
+    exactly); linear discharge everywhere, and in the upper triangle f of
+    quad (1, 1) an added discharge along the diagonal's normal that grows
+    from 0 at one end of the shared edge to its maximum at the other: the
+    wave speed of the shared edge peaks at that endpoint, on f's side."""
+    hb0, xi0 = 10.0, 0.05
+    e_v, f_v = _lower_triangle(1, 1), _upper_triangle(1, 1)
+    P, Q = e_v[1], e_v[2]                      # edge 0 of e: from a2 to a3
+    d = Q - P
+    n = np.array([d[1], -d[0]]) / np.hypot(*d)  # outward normal of e
+    A = 60.0
+
+    def U(x, y):
+        return 0.3 + 0.1 * y
+
+    def V(x, y):
+        return -0.2 + 0.05 * x
+
+    def ramp(x, y):
+        return ((x - P[0]) * d[0] + (y - P[1]) * d[1]) / (d @ d)
+    return dict(hb0=hb0, xi0=xi0, e_v=e_v, f_v=f_v, P=P, Q=Q, n=n, U=U, V=V,
+                Uf=lambda x, y: U(x, y) + A * n[0] * ramp(x, y),
+                Vf=lambda x, y: V(x, y) + A * n[1] * ramp(x, y))
+
+
+def _lam_oracle_delta(oracle_mod, c, lib=None):
+    """oracle RHS of element e (lower triangle of quad (1,1)) with f's
+    discharge modified, minus the RHS with the unmodified linear state"""
+    o = oracle_mod.Oracle(_LAM_N, _LAM_N, 1, bc="reflective", Lx=_LAM_L, Ly=_LAM_L, g=_LAM_G, lib=lib)
+    E = o.E
+    e = 2 * (1 * _LAM_N + 1)
+    f = e + 1
+    hb = np.zeros((E, 3))
+    xi = np.zeros((E, 3))
+    U = np.zeros((E, 3))
+    V = np.zeros((E, 3))
+    verts, _, nb = o.geometry()
+    assert nb[e, 0] == f
+    assert np.allclose(verts[e], c["e_v"]) and np.allclose(verts[f], c["f_v"])
+    for k in range(E):
+        hb[k] = _p1_coefficients(lambda x, y: c["hb0"], verts[k])
+        xi[k] = _p1_coefficients(lambda x, y: c["xi0"], verts[k])
+        U[k] = _p1_coefficients(c["U"], verts[k])
+        V[k] = _p1_coefficients(c["V"], verts[k])
+    R0 = o.rhs(hb, xi, U, V)[:, e]
+    U[f] = _p1_coefficients(c["Uf"], verts[f])
+    V[f] = _p1_coefficients(c["Vf"], verts[f])
+    R1 = o.rhs(hb, xi, U, V)[:, e]
+    return R1 - R0
+
+
+def _lam_numpy_delta(c, points=(0.0, 0.5, 1.0), sides=("in", "out")):
+    """the same difference from one edge integral, evaluated here: element
+    e's volume term and its other two edges are unchanged, so
+    d R_e = -(1 / |det B_e|) (int F^(modified) phi - int F^(linear) phi)"""
+    g, H = _LAM_G, c["hb0"] + c["xi0"]
+    P, Q, n = c["P"], c["Q"], c["n"]
+    length = np.hypot(*(Q - P))
+    s_q, w_q = np.polynomial.legendre.leggauss(6)
+    s_q, w_q = 0.5 * (s_q + 1.0), 0.5 * w_q
+    pres = 0.5 * g * c["xi0"] * (c["xi0"] + 2 * c["hb0"])
+
+    def flux(Uq, Vq):
+        un = (Uq * n[0] + Vq * n[1]) / H
+        return np.array([Uq * n[0] + Vq * n[1], Uq * un + pres * n[0], Vq * un + pres * n[1]])
+
+    def speed(Uq, Vq):
+        return abs((Uq * n[0] + Vq * n[1]) / H) + np.sqrt(g * H)
+
+    def integral(Uf, Vf):
+        lam = 0.0
+        for s in points:
+            x, y = P + s * (Q - P)
+            if "in" in sides:
+                lam = max(lam, speed(c["U"](x, y), c["V"](x, y)))
+            if "out" in sides:
+                lam = max(lam, speed(Uf(x, y), Vf(x, y)))
+        acc = np.zeros((3, 3))
+        for s, w in zip(s_q, w_q):
+            x, y = P + s * (Q - P)
+            cm = np.array([c["xi0"], c["U"](x, y), c["V"](x, y)])
+            cp = np.array([c["xi0"], Uf(x, y), Vf(x, y)])
+            F = 0.5 * (flux(cm[1], cm[2]) + flux(cp[1], cp[2])) + 0.5 * lam * (cm - cp)
+            acc += w * length * np.outer(F, _p1_basis_at(c["e_v"], x, y))
+        return acc, lam
+    I1, lam1 = integral(c["Uf"], c["Vf"])
+    I0, _ = integral(c["U"], c["V"])
+    det = abs(np.linalg.det(np.array([c["e_v"][1] - c["e_v"][0], c["e_v"][2] - c["e_v"][0]]).T))
+    return -(I1 - I0) / det, lam1
+
+
+def test_lf_wave_speed_three_points_both_sides(oracle_mod):
+    """λ of the Lax-Friedrichs flux is the maximum over both sides and
+    s = 0, 1/2, 1: the oracle's RHS change equals the independent one-edge
+    evaluation, and the construction makes the two plausible misreadings
+    (midpoint only, interior side only) differ from it clearly."""
+    c = _lam_case()
+    ref, lam = _lam_numpy_delta(c)
+    _, lam_mid = _lam_numpy_delta(c, points=(0.5,))
+    _, lam_in = _lam_numpy_delta(c, sides=("in",))
+    assert lam > 1.15 * lam_mid and lam > 1.15 * lam_in, (lam, lam_mid, lam_in)
+    got = _lam_oracle_delta(oracle_mod, c)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max(), (got, ref)
+    for pts, sd in (((0.5,), ("in", "out")), ((0.0, 0.5, 1.0), ("in",))):
+        wrong, _ = _lam_numpy_delta(c, points=pts, sides=sd)
+        assert np.abs(wrong - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+# the lines of the oracle's wave-speed loop that the planted mistakes change
+_LAM_LOOP = "for (int k = 0; k < 3; ++k) {\n      double s = 0.5 * k;"
+_LAM_OUTER = "      if (lb > lam) lam = lb;\n"
+
+
+@pytest.mark.parametrize("mutation", ["midpoint_only", "interior_only"])
+def test_lf_wave_speed_pin_catches_planted_mistakes(oracle_mod, tmp_path, mutation):
+    """A copy of the oracle with λ taken at the edge midpoint only, or from
+    the interior side only, fails the comparison above."""
+    src = oracle_mod.source()
+    assert src.count(_LAM_LOOP) == 1 and src.count(_LAM_OUTER) == 1
+    if mutation == "midpoint_only":
+        src = src.replace(_LAM_LOOP, "for (int k = 1; k < 2; ++k) {\n      double s = 0.5 * k;")
+    else:
+        src = src.replace(_LAM_OUTER, "")
+    lib = oracle_mod.build_variant(src, mutation, str(tmp_path))
+    c = _lam_case()
+    ref, _ = _lam_numpy_delta(c)
+    got = _lam_oracle_delta(oracle_mod, c, lib=lib)
+    assert np.abs(got - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- diagnostics
+def _linear_square_integral(a, b, c, Lx, Ly):
+    """exact integral of (a + b x + c y)^2 over [0, Lx] x [0, Ly]:
+    area (mean^2 + b^2 Lx^2 / 12 + c^2 Ly^2 / 12)"""
+    mean = a + b * Lx / 2 + c * Ly / 2
+    return Lx * Ly * (mean ** 2 + (b * Lx) ** 2 / 12 + (c * Ly) ** 2 / 12)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_energy_diagnostic_closed_form(oracle_mod, p):
+    """energy = 1/2 integral (g xi^2 + U u + V v) and mass = integral xi, at
+    rest, in uniform flow and with linear fields at constant depth (then
+    u = q / H exactly): E = 1/2 (g int xi^2 + int (U^2 + V^2) / H)."""
+    Lx, Ly, g, H0 = 1.2, 0.8, 9.81, 7.5
+    o = oracle_mod.Oracle(3, 4, p, bc="reflective", Lx=Lx, Ly=Ly, g=g)
+    cases = [((0.3, 0, 0), (0, 0, 0), (0, 0, 0)),            # at rest
+             ((0.3, 0, 0), (0.9, 0, 0), (-0.4, 0, 0)),       # uniform flow
+             ((0.2, 0.5, -0.3), (0.6, -0.7, 0.4), (0.1, 0.3, 0.8))]
+    for (xa, xb, xc), (ua, ub, uc), (va, vb, vc) in cases:
+        hb = o.project_hb(lambda x, y: H0 - (xa + xb * x + xc * y))
+        xi = o.project(lambda x, y: xa + xb * x + xc * y)
+        U = o.project(lambda x, y: ua + ub * x + uc * y)
+        V = o.project(lambda x, y: va + vb * x + vc * y)
+        mass, energy = o.diagnostics(hb, xi, U, V)
+        m_ref = Lx * Ly * (xa + xb * Lx / 2 + xc * Ly / 2)
+        e_ref = 0.5 * (g * _linear_square_integral(xa, xb, xc, Lx, Ly) +
+                       (_linear_square_integral(ua, ub, uc, Lx, Ly) +
+                        _linear_square_integral(va, vb, vc, Lx, Ly)) / H0)
+        assert abs(mass - m_ref) <= 1e-13 * abs(m_ref)
+        assert abs(energy - e_ref) <= 1e-13 * e_ref, (energy, e_ref)
+
+
+_EN_HALF = "en += 0.5 * w *"
+_EN_UU = "eval_field(h, U, e, xr, yr) * eval_field(h, u, e, xr, yr)"
+
+
+@pytest.mark.parametrize("mutation", ["no_half", "U_times_U"])
+def test_energy_pin_catches_planted_mistakes(oracle_mod, tmp_path, mutation):
+    """A copy of the oracle whose energy drops the factor 1/2, or uses U^2
+    instead of U u, fails the closed form of the uniform flow."""
+    src = oracle_mod.source()
+    assert src.count(_EN_HALF) == 1 and src.count(_EN_UU) == 1
+    if mutation == "no_half":
+        src = src.replace(_EN_HALF, "en += w *")
+    else:
+        src = src.replace(_EN_UU, "eval_field(h, U, e, xr, yr) * eval_field(h, U, e, xr, yr)")
+    lib = oracle_mod.build_variant(src, mutation, str(tmp_path))
+    Lx, Ly, g, H0, xi0, U0 = 1.2, 0.8, 9.81, 7.5, 0.3, 0.9
+    o = oracle_mod.Oracle(3, 4, 2, bc="reflective", Lx=Lx, Ly=Ly, g=g, lib=lib)
+    hb = o.project_hb(lambda x, y: H0 - xi0 + 0 * x)
+    xi = o.project(lambda x, y: xi0 + 0 * x)
+    U = o.project(lambda x, y: U0 + 0 * x)
+    _, energy = o.diagnostics(hb, xi, U, np.zeros_like(U))
+    e_ref = 0.5 * Lx * Ly * (g * xi0 ** 2 + U0 ** 2 / H0)
+    assert abs(energy - e_ref) > 1e-3 * e_ref
