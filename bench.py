@@ -258,7 +258,7 @@ def run_batch(args, wls):
         cfgs.append(cfg)
         for k in range(4):
             fields[k].append(f[k])
-    b = B.dg_batch_init(cfgs, *fields, stream=stream)
+    b = B.dg_batch_init_device(cfgs, *fields, stream=stream)
     del fields
     torch.cuda.empty_cache()
     S = wls[0].rk_order

@@ -121,15 +121,21 @@ typedef struct {
 
 typedef struct dg_ctx dg_ctx;
 
-/* Number of basis functions K = (p+1)(p+2)/2 (0 for p outside 0..4). */
+/* Number of basis functions K = (p+1)(p+2)/2 of P^p on a triangle (paper
+ * §2.2, the counts K = 1, 3, 6, 10 of the printed basis; p = 4 continues the
+ * basis, which the paper prints up to order 3); 0 for p outside 0..4. */
 int dg_num_basis(int p);
 
-/* Number of bathymetry coefficients Kb per element: h_b is a DG field of
- * P^max(p,1) (at p = 0 a piecewise-constant h_b would drop the source
- * g xi grad h_b of Eq. (5)), so Kb = K for p >= 1 and 3 for p = 0. */
+/* Number of bathymetry coefficients Kb per element (h_b enters the source
+ * r(c) of Eq. (5) and the pressure term of Eq. (16); the paper leaves its
+ * representation open): h_b is a DG field of P^max(p,1) (at
+ * p = 0 a piecewise-constant h_b would drop the source g xi grad h_b), so
+ * Kb = K for p >= 1 and 3 for p = 0. */
 int dg_num_basis_bathymetry(int p);
 
-/* Number of triangles 2 nx ny of a configuration (0 if invalid). */
+/* Number of triangles 2 nx ny of a configuration: each quad of the
+ * block-structured grid is split into two triangles (paper §2.3); 0 if
+ * invalid. */
 long long dg_num_elements(const dg_config* cfg);
 
 /* Create a context (paper §2.2 discrete unknowns c_ei, Eqs. (13)-(14)).
@@ -142,9 +148,10 @@ long long dg_num_elements(const dg_config* cfg);
 dg_status dg_init(const dg_config* cfg, const double* hb, const double* xi, const double* qx,
                   const double* qy, void* stream, dg_ctx** out);
 
-/* As dg_init, but hb, xi, qx, qy are DEVICE arrays, FP64 SoA [Kb][E] (h_b)
- * and [K][E] (one field each), e.g. the output of dg_project.  They are
- * copied. */
+/* As dg_init (paper §2.2, Eqs. (13)-(14)), but hb, xi, qx, qy are DEVICE
+ * arrays, FP64 SoA [Kb][E] (h_b) and [K][E] (one field each), e.g. the
+ * output of dg_project.  They are copied; the caller keeps ownership.
+ * Errors: DG_ERR_ARG, DG_ERR_UNSUPPORTED, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_xi, const void* d_qx,
                          const void* d_qy, void* stream, dg_ctx** out);
 
@@ -157,37 +164,65 @@ dg_status dg_init_device(const dg_config* cfg, const void* d_hb, const void* d_x
  * does not touch the error state that dg_run reports. */
 dg_status dg_rhs(dg_ctx* ctx, const void* d_state_in, void* d_rhs_out);
 
-/* One SSP-RK step of the context's state.  If dt_used is not NULL the stream
- * is synchronised and *dt_used receives the step's dt. */
+/* One SSP-RK step of the context's state (the paper states no time
+ * integrator, §3.1 uses a fixed dt; this library takes SSP Runge-Kutta in
+ * Shu-Osher form, each stage w' = a w0 + b (w + dt R(w)) with R of dg_rhs).  Launched
+ * asynchronously on the context's stream.  If dt_used is not NULL the stream
+ * is synchronised and *dt_used receives the step's dt.  Dry or non-finite
+ * states are flagged on the device and reported by the next dg_run.
+ * Errors: DG_ERR_ARG (ctx NULL), DG_ERR_CUDA. */
 dg_status dg_rk_step(dg_ctx* ctx, double* dt_used);
 
-/* nsteps SSP-RK steps, each launched as one captured CUDA graph.  Synchronises
- * the stream once at the end, reads the device error word and (if t_out is not
- * NULL) the simulation time.  Returns DG_ERR_DRY / DG_ERR_NONFINITE if a
- * kernel flagged one. */
+/* nsteps SSP-RK steps (as dg_rk_step), each launched as one
+ * captured CUDA graph; nsteps = 0 only reads the error word and time.
+ * Synchronises the stream once at the end, reads the device error word and
+ * (if t_out is not NULL) the simulation time.  Returns DG_ERR_DRY (H <= 0 met;
+ * the paper does not treat dry cells) or DG_ERR_NONFINITE if a kernel flagged one since the last
+ * report; the word is then cleared and the context stays usable.
+ * Errors: DG_ERR_ARG (ctx NULL, nsteps < 0), DG_ERR_DRY, DG_ERR_NONFINITE,
+ * DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_run(dg_ctx* ctx, int nsteps, double* t_out);
 
-/* Copy the state to host FP64 AoS arrays [E][K] (each may be NULL). */
+/* Copy the state, the coefficients c_ei of xi, q_x, q_y (paper §2.2,
+ * Eqs. (13)-(14)), to host FP64 AoS arrays [E][K] (each may be NULL; the
+ * caller owns them).  Synchronises the stream.
+ * Errors: DG_ERR_ARG, DG_ERR_OOM (staging buffer), DG_ERR_CUDA. */
 dg_status dg_get_state(dg_ctx* ctx, double* xi, double* qx, double* qy);
 
-/* Replace the state (host FP64 AoS [E][K]) and the time. */
+/* Replace the state (coefficients of Eqs. (13)-(14), host FP64 AoS [E][K],
+ * all three required, copied) and the time t.  The next step re-evaluates
+ * the new state.  Synchronises the stream.
+ * Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_set_state(dg_ctx* ctx, const double* xi, const double* qx, const double* qy, double t);
 
-/* Device pointer of the context's state, SoA [3][K][E] in its precision. */
+/* Device pointer of the context's state (coefficients of Eqs. (13)-(14)),
+ * SoA [3][K][E] in its precision; owned by the context, valid until
+ * dg_destroy.  Errors: DG_ERR_ARG. */
 dg_status dg_state_device(dg_ctx* ctx, void** d_state);
 
-/* mass = sum_e integral xi; energy = 1/2 sum_e integral (g xi^2 + U u + V v),
- * both accumulated in FP64 in a fixed order (deterministic). */
+/* mass = sum_e integral xi (the quantity the continuity equation of Eq. (1)
+ * conserves, paper §2.1); energy = 1/2 sum_e integral (g xi^2 + U u + V v)
+ * with u from the projection of Eq. (12) (not in the paper: the usual
+ * shallow-water energy relative to the rest state), both accumulated in
+ * FP64 in a fixed order (deterministic).  Synchronises the stream.
+ * Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_diagnostics(dg_ctx* ctx, double* mass, double* energy);
 
-/* Set-up projection (not on the time-stepping path): nodes of the library's
- * Gauss rule on every element, so that a caller can sample any function there
- * and L2-project it.  dg_proj_num_nodes gives Q; dg_proj_nodes writes device
- * FP64 [2][Q][E] (x then y); dg_project turns device FP64 samples [Q][E] into
- * device FP64 SoA coefficients [K][E].  Asynchronous on stream. */
+/* Set-up projection (not on the time-stepping path; the paper does not state
+ * how initial data are projected; this is the L2 projection onto the basis
+ * of §2.2): nodes of the library's Gauss rule on every element, so that
+ * a caller can sample any function there and L2-project it.
+ * dg_proj_num_nodes gives Q (0 for p outside 0..4); dg_proj_nodes writes
+ * device FP64 [2][Q][E] (x then y); dg_project turns device FP64 samples
+ * [Q][E] into device FP64 SoA coefficients [K][E].  Caller-owned device
+ * arrays; asynchronous on stream.  Errors: DG_ERR_ARG, DG_ERR_CUDA. */
 int dg_proj_num_nodes(int p);
 dg_status dg_proj_nodes(const dg_config* cfg, void* d_xy, void* stream);
 dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, void* stream);
+
+/* Flag bits that dg_rhs_noalloc ORs into the caller's optional word. */
+enum { DG_FLAG_DRY = 1u /* a non-positive (or NaN) depth at a wave-speed point, or a velocity-projection
+                           matrix that is not positive definite: the result is not meaningful */ };
 
 /* dg_rhs_noalloc: the same right-hand side as dg_rhs, computed without
  * allocating any device memory.  The paper has no counterpart; this is an
@@ -202,21 +237,29 @@ dg_status dg_project(const dg_config* cfg, const void* d_vals, void* d_coef, voi
  *               Kb = dg_num_basis_bathymetry(p).
  *   d_state_in: device SoA [3][K][E] state in cfg's precision (input).
  *   d_rhs_out:  device SoA [3][K][E] (output), must not overlap d_state_in.
+ *   d_flags:    NULL, or a caller-owned device word into which the call ORs
+ *               DG_FLAG_DRY (stream-ordered; the call does not clear it, so
+ *               the caller zeroes it and reads it after synchronising).  With
+ *               NULL a dry state is not reported: the call returns DG_OK and
+ *               the output holds whatever the arithmetic gave.
  *   stream:     cudaStream_t or NULL; the call is asynchronous on it.
  * Intermediates live in one fixed 32 MiB array inside the library's device
  * image, reserved on every GPU that loads the library until the process
  * exits.  A mesh needs about (K + 3(p+1) + p(p+1) + 3K + 3(6p+7)) words per
- * triangle, plus 2K^2 in FP64 (8 bytes FP64, 4 bytes FP32, each block rounded
- * up to 256 bytes); meshes that do not fit are rejected with DG_ERR_ARG before
- * any GPU work (about 24,000 triangles at p = 2 in FP64).  The first call on a device looks
- * up the array's device address once (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Every call shares the array, which keeps
- * the previous call's contents (the error word is cleared per call); calls
- * whose GPU work overlaps race and give wrong results.
+ * triangle, plus 2K^2 in FP64, plus K(K+1)/2 FP64 words with DG_PROJ_MIXED
+ * (8 bytes FP64, 4 bytes FP32, each block rounded up to 256 bytes); meshes
+ * that do not fit are rejected with DG_ERR_ARG before any GPU work (about
+ * 24,000 triangles at p = 2 in FP64).  The first call on a device looks up
+ * the array's device address once (cudaGetSymbolAddress) and caches it; make
+ * that first call before any stream capture.  A cudaDeviceReset() unloads
+ * the array with the library's device image: do not call this entry point on
+ * a device after resetting it.  Every call shares the array, which keeps the
+ * previous call's contents; calls whose GPU work overlaps race and give wrong
+ * results.
  * Errors: DG_ERR_ARG (invalid or too large), DG_ERR_UNSUPPORTED (forcing),
  * DG_ERR_CUDA. */
 dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_state_in, void* d_rhs_out,
-                         void* stream);
+                         unsigned* d_flags, void* stream);
 
 /* ---- batched instances -------------------------------------------------
  * Many independent problems of uneven size and order (ensembles of
@@ -227,49 +270,72 @@ dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_s
  * element code), so results equal those of separate dg_init contexts. */
 typedef struct dg_batch dg_batch;
 
-/* n instances; cfgs[i] as for dg_init with p = 1..3, nx, ny >= 2, uniform
- * meshes without forcing (else DG_ERR_UNSUPPORTED).  All
- * instances share precision, proj_precision, rk_order and fixed-vs-CFL time
- * stepping (else DG_ERR_ARG).  d_hb[i], d_xi[i], d_qx[i], d_qy[i]: DEVICE
- * FP64 SoA [K_i][E_i] arrays (copied).  Errors: DG_ERR_ARG,
- * DG_ERR_UNSUPPORTED (p = 0 or 4, Dirichlet), DG_ERR_OOM, DG_ERR_CUDA. */
-dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
-                        const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out);
+/* n instances of the scheme of paper §2.2 (the initial coefficients of
+ * Eqs. (13)-(14) per instance; batching is not in the paper).  cfgs[i] as
+ * for dg_init with p = 1..3, nx, ny >= 2, uniform meshes without forcing
+ * (else DG_ERR_UNSUPPORTED).  All instances share precision,
+ * proj_precision, rk_order and fixed-vs-CFL time stepping (else
+ * DG_ERR_ARG).  hb[i], xi[i], qx[i], qy[i]: HOST FP64 AoS arrays [E_i][K_i]
+ * (as for dg_init; caller-owned, copied: each instance is transposed and
+ * uploaded through one reused staging buffer).  Synchronises the stream.
+ * Errors: DG_ERR_ARG (checked before any CUDA call), DG_ERR_UNSUPPORTED
+ * (p = 0 or 4, Dirichlet, general meshes, forcing), DG_ERR_OOM,
+ * DG_ERR_CUDA. */
+dg_status dg_batch_init(int n, const dg_config* cfgs, const double* const* hb, const double* const* xi,
+                        const double* const* qx, const double* const* qy, void* stream, dg_batch** out);
 
-/* nsteps steps of every instance; t_out (NULL or n doubles) receives each
- * instance's time.  Synchronises the stream once at the end. */
+/* As dg_batch_init, but d_hb[i], d_xi[i], d_qx[i], d_qy[i] are DEVICE FP64
+ * SoA [K_i][E_i] arrays (e.g. the output of dg_project; caller-owned,
+ * copied).  The resulting batch is identical to the host form's. */
+dg_status dg_batch_init_device(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
+                               const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out);
+
+/* nsteps SSP-RK steps (the time stepping of dg_rk_step) of every instance,
+ * each with its own CFL step; t_out (NULL or n doubles) receives each
+ * instance's time.  Synchronises the stream once at the end and reports
+ * DG_ERR_DRY / DG_ERR_NONFINITE as dg_run does.  Errors: DG_ERR_ARG,
+ * DG_ERR_DRY, DG_ERR_NONFINITE, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out);
 
-/* state of instance i as host FP64 AoS [E_i][K_i] arrays (each may be NULL;
- * page-locked buffers make the copies faster).  Synchronises the stream. */
+/* state of instance i (coefficients of Eqs. (13)-(14)) as host FP64 AoS
+ * [E_i][K_i] arrays (each may be NULL; page-locked buffers make the copies
+ * faster).  Synchronises the stream.  Errors: DG_ERR_ARG, DG_ERR_OOM,
+ * DG_ERR_CUDA. */
 dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy);
 
-/* replace the state of instance i (host FP64 AoS [E_i][K_i] arrays, all three
- * required) and its model time t; the next dg_batch_run re-evaluates the
- * batch.  Synchronises the stream.  Errors: DG_ERR_ARG, DG_ERR_OOM,
- * DG_ERR_CUDA. */
+/* replace the state of instance i (coefficients of Eqs. (13)-(14), host FP64
+ * AoS [E_i][K_i] arrays, all three required) and its model time t; the next
+ * dg_batch_run re-evaluates the batch.  Synchronises the stream.
+ * Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double* qx, const double* qy, double t);
 
-/* Autotuner: times trial_steps steps with 32, 64, 96 and 128 elements per
+/* Autotuner of the batched launch (not in the paper; it changes only the
+ * launch shape, never the arithmetic): times trial_steps steps with 32, 64,
+ * 96 and 128 elements per
  * work item (one thread per element), restoring the state after each, and
  * keeps the fastest; *block_out (may be NULL) receives it and ms_out (NULL or
  * 4 doubles) the ms per step of each.  State and times are unchanged on
  * return.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out);
 
-/* set the elements per work item (32, 64, 96 or 128; DG_ERR_ARG otherwise);
- * on any error the batch keeps its previous setting */
+/* set the elements per work item of the batched launch (not in the paper;
+ * 32, 64, 96 or 128; DG_ERR_ARG otherwise); on any error the batch keeps its
+ * previous setting.  Synchronises the stream. */
 dg_status dg_batch_set_block(dg_batch* b, int block);
 
-/* degrees of freedom updated per RK stage: sum over instances of 3 K E */
+/* degrees of freedom updated per RK stage: sum over instances of 3 K E (the
+ * coefficients of xi, q_x, q_y of Eqs. (13)-(14)); 0 for NULL */
 long long dg_batch_dofs(const dg_batch* b);
 
+/* Release every resource of the batch (NULL is ignored); synchronises its
+ * stream first. */
 void dg_batch_destroy(dg_batch* b);
 
-/* Release every resource of the context (NULL is ignored). */
+/* Release every resource of the context (NULL is ignored); synchronises its
+ * stream first. */
 void dg_destroy(dg_ctx* ctx);
 
-/* Static string naming a status. */
+/* Static string naming a status ("DG_ERR_UNKNOWN" for other values). */
 const char* dg_status_str(dg_status s);
 
 #ifdef __cplusplus

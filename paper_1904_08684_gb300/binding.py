@@ -26,7 +26,7 @@ PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
 EXPORTS = ["dg_num_basis", "dg_num_basis_bathymetry", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
            "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc",
-           "dg_batch_init", "dg_batch_run", "dg_batch_get_state", "dg_batch_set_state", "dg_batch_autotune",
+           "dg_batch_init", "dg_batch_init_device", "dg_batch_run", "dg_batch_get_state", "dg_batch_set_state", "dg_batch_autotune",
            "dg_batch_set_block", "dg_batch_dofs", "dg_batch_destroy"]
 
 
@@ -102,9 +102,11 @@ def load(build_if_missing=True):
     lib.dg_proj_num_nodes.argtypes = [ctypes.c_int]
     lib.dg_proj_nodes.argtypes = [cp, vp, vp]
     lib.dg_project.argtypes = [cp, vp, vp, vp]
-    lib.dg_rhs_noalloc.argtypes = [cp, vp, vp, vp, vp]
+    lib.dg_rhs_noalloc.argtypes = [cp, vp, vp, vp, vp, vp]
     vpp = ctypes.POINTER(ctypes.c_void_p)
-    lib.dg_batch_init.argtypes = [ctypes.c_int, cp, vpp, vpp, vpp, vpp, vp, ctypes.POINTER(vp)]
+    dpp = ctypes.POINTER(ctypes.POINTER(ctypes.c_double))
+    lib.dg_batch_init.argtypes = [ctypes.c_int, cp, dpp, dpp, dpp, dpp, vp, ctypes.POINTER(vp)]
+    lib.dg_batch_init_device.argtypes = [ctypes.c_int, cp, vpp, vpp, vpp, vpp, vp, ctypes.POINTER(vp)]
     lib.dg_batch_run.argtypes = [vp, ctypes.c_int, dp]
     lib.dg_batch_get_state.argtypes = [vp, ctypes.c_int, dp, dp, dp]
     lib.dg_batch_set_state.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_double]
@@ -253,10 +255,14 @@ def dg_project(cfg, d_vals, d_coef, stream=None):
     _check(load().dg_project(ctypes.byref(cfg), _dptr(d_vals), _dptr(d_coef), _stream(stream)), "dg_project")
 
 
-def dg_rhs_noalloc(cfg, d_hb, d_state_in, d_rhs_out, stream=None):
-    """dg_rhs without device allocation (fixed in-library scratch array)."""
+DG_FLAG_DRY = 1
+
+
+def dg_rhs_noalloc(cfg, d_hb, d_state_in, d_rhs_out, d_flags=None, stream=None):
+    """dg_rhs without device allocation (fixed in-library scratch array);
+    d_flags: None or a device int32 word the call ORs DG_FLAG_DRY into."""
     _check(load().dg_rhs_noalloc(ctypes.byref(cfg), _dptr(d_hb), _dptr(d_state_in), _dptr(d_rhs_out),
-                                 _stream(stream)), "dg_rhs_noalloc")
+                                 _dptr(d_flags), _stream(stream)), "dg_rhs_noalloc")
 
 
 def _ptr_array(ts):
@@ -266,13 +272,34 @@ def _ptr_array(ts):
     return arr
 
 
-def dg_batch_init(cfgs, d_hb, d_xi, d_qx, d_qy, stream=None):
+def dg_batch_init(cfgs, hb, xi, qx, qy, stream=None):
+    """Batch of instances from host FP64 (E_i, K_i) arrays (lists)."""
+    n = len(cfgs)
+    carr = (dg_config * n)(*cfgs)
+    keep = []
+    arrs = []
+    for lst in (hb, xi, qx, qy):
+        ptrs = (ctypes.POINTER(ctypes.c_double) * n)()
+        for k, (cfg, a) in enumerate(zip(cfgs, lst)):
+            nb = dg_num_basis_bathymetry(cfg.p) if lst is hb else dg_num_basis(cfg.p)
+            a = _host(a, dg_num_elements(cfg), nb)
+            keep.append(a)
+            ptrs[k] = _hptr(a)
+        arrs.append(ptrs)
+    h = ctypes.c_void_p()
+    _check(load().dg_batch_init(n, carr, *arrs, _stream(stream), ctypes.byref(h)), "dg_batch_init")
+    h._n = n
+    return h
+
+
+def dg_batch_init_device(cfgs, d_hb, d_xi, d_qx, d_qy, stream=None):
     """Batch of instances from device FP64 (K_i, E_i) arrays (lists)."""
     n = len(cfgs)
     carr = (dg_config * n)(*cfgs)
     h = ctypes.c_void_p()
-    _check(load().dg_batch_init(n, carr, _ptr_array(d_hb), _ptr_array(d_xi), _ptr_array(d_qx),
-                                _ptr_array(d_qy), _stream(stream), ctypes.byref(h)), "dg_batch_init")
+    _check(load().dg_batch_init_device(n, carr, _ptr_array(d_hb), _ptr_array(d_xi), _ptr_array(d_qx),
+                                       _ptr_array(d_qy), _stream(stream), ctypes.byref(h)),
+           "dg_batch_init_device")
     h._n = n
     return h
 

@@ -255,22 +255,69 @@ dg_status validate_one(const dg_config* c) {
   return DG_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
-                        const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out) {
-  dgswe::NvtxRange nvtx_range("dg_batch_init");
-  if (n < 1 || !cfgs || !d_hb || !d_xi || !d_qx || !d_qy || !out) return DG_ERR_ARG;
+// Checks shared by both forms of dg_batch_init (no CUDA call).
+dg_status validate_batch(int n, const dg_config* cfgs, const void* const* hb, const void* const* xi,
+                         const void* const* qx, const void* const* qy, dg_batch** out) {
+  if (n < 1 || !cfgs || !hb || !xi || !qx || !qy || !out) return DG_ERR_ARG;
   for (int i = 0; i < n; ++i) {
     dg_status s = validate_one(&cfgs[i]);
     if (s != DG_OK) return s;
-    if (!d_hb[i] || !d_xi[i] || !d_qx[i] || !d_qy[i]) return DG_ERR_ARG;
+    if (!hb[i] || !xi[i] || !qx[i] || !qy[i]) return DG_ERR_ARG;
     if (cfgs[i].precision != cfgs[0].precision || cfgs[i].proj_precision != cfgs[0].proj_precision ||
         cfgs[i].rk_order != cfgs[0].rk_order || (cfgs[i].dt > 0.0) != (cfgs[0].dt > 0.0))
       return DG_ERR_ARG;
   }
+  return DG_OK;
+}
+
+// Source of one instance's FP64 input fields on the device, SoA [Kb][E]
+// (h_b) and [K][E] (xi, qx, qy): the caller's device arrays, or the caller's
+// host AoS arrays transposed and uploaded into one staging buffer that is
+// reused for every instance (stream order keeps the previous instance's
+// conversion ahead of the next upload).
+struct InputSource {
+  const void* const* f[4];
+  bool host;
+  double* stage;
+  size_t stage_n;
+  dg_status get(int i, long long E, int K, int KB, const double* out[4], cudaStream_t s) {
+    if (!host) {
+      for (int k = 0; k < 4; ++k) out[k] = static_cast<const double*>(f[k][i]);
+      return DG_OK;
+    }
+    const size_t need = (size_t)(KB + 3 * K) * (size_t)E;
+    if (stage_n < need) {
+      CK(cudaStreamSynchronize(s));
+      if (stage) cudaFree(stage);
+      stage = nullptr;
+      stage_n = 0;
+      CK(cudaMalloc((void**)&stage, sizeof(double) * need));
+      stage_n = need;
+    }
+    std::vector<double> t;
+    try {
+      t.resize(need);
+    } catch (const std::exception&) {   // no C++ exception crosses the C ABI
+      return DG_ERR_OOM;
+    }
+    size_t off = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int nk = k == 0 ? KB : K;
+      const double* h = static_cast<const double*>(f[k][i]);
+      for (long long e = 0; e < E; ++e)
+        for (int c = 0; c < nk; ++c) t[off + (size_t)c * E + e] = h[(size_t)e * nk + c];
+      out[k] = stage + off;
+      off += (size_t)nk * E;
+    }
+    // the previous instance's kernels read the staging buffer: they run
+    // first on this stream, and the copy below waits for them
+    CK(cudaMemcpyAsync(stage, t.data(), sizeof(double) * need, cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    return DG_OK;
+  }
+};
+
+dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* stream, dg_batch** out) {
   dg_batch* b = new (std::nothrow) dg_batch();
   if (!b) return DG_ERR_OOM;
   std::vector<BatchInst> desc;
@@ -379,11 +426,13 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
     d.p = h.p;
     const long long KE = (long long)h.K * h.E;
     char* w0 = (char*)d.w[0];
-    if ((st = store_real(b, (const double*)d_xi[i], w0, KE, s)) != DG_OK) break;
-    if ((st = store_real(b, (const double*)d_qx[i], w0 + KE * b->rsz, KE, s)) != DG_OK) break;
-    if ((st = store_real(b, (const double*)d_qy[i], w0 + 2 * KE * b->rsz, KE, s)) != DG_OK) break;
+    const double* in[4];
+    if ((st = src.get(i, h.E, h.K, h.K, in, s)) != DG_OK) break;
+    if ((st = store_real(b, in[1], w0, KE, s)) != DG_OK) break;
+    if ((st = store_real(b, in[2], w0 + KE * b->rsz, KE, s)) != DG_OK) break;
+    if ((st = store_real(b, in[3], w0 + 2 * KE * b->rsz, KE, s)) != DG_OK) break;
     void *ph = (void*)d.hb, *pt = (void*)d.hbt, *pg = (void*)d.ghb, *pl = (void*)d.lin;
-    const double* hbi = (const double*)d_hb[i];
+    const double* hbi = in[0];
     switch (b->arith) {
       case ARITH_FP64: e = static_fp64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, pl, s); break;
       case ARITH_FP32_P64: e = static_fp32p64(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
@@ -408,6 +457,35 @@ dg_status dg_batch_init(int n, const dg_config* cfgs, const void* const* d_hb, c
   }
   *out = b;
   return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_batch_init(int n, const dg_config* cfgs, const double* const* hb, const double* const* xi,
+                        const double* const* qx, const double* const* qy, void* stream, dg_batch** out) {
+  dgswe::NvtxRange nvtx_range("dg_batch_init");
+  const void* const* f[4] = {(const void* const*)hb, (const void* const*)xi, (const void* const*)qx,
+                             (const void* const*)qy};
+  dg_status s = validate_batch(n, cfgs, f[0], f[1], f[2], f[3], out);
+  if (s != DG_OK) return s;
+  InputSource src = {{f[0], f[1], f[2], f[3]}, true, nullptr, 0};
+  s = batch_create(n, cfgs, src, stream, out);
+  if (src.stage) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(src.stage);
+  }
+  return s;
+}
+
+dg_status dg_batch_init_device(int n, const dg_config* cfgs, const void* const* d_hb, const void* const* d_xi,
+                               const void* const* d_qx, const void* const* d_qy, void* stream, dg_batch** out) {
+  dgswe::NvtxRange nvtx_range("dg_batch_init_device");
+  dg_status s = validate_batch(n, cfgs, d_hb, d_xi, d_qx, d_qy, out);
+  if (s != DG_OK) return s;
+  InputSource src = {{d_hb, d_xi, d_qx, d_qy}, false, nullptr, 0};
+  return batch_create(n, cfgs, src, stream, out);
 }
 
 void dg_batch_destroy(dg_batch* b) {

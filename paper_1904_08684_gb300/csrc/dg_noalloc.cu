@@ -13,9 +13,18 @@
 // routine; the caller passes the bathymetry, the state and the output.
 //
 // The array is shared by every call on a device and keeps the previous
-// call's contents; the error word is cleared at the start of each call.
+// call's contents; its error word is cleared at the start of each call.
 // Calls whose GPU work overlaps (different streams or threads, no ordering
-// between them) race on the array and produce wrong results.
+// between them) race on the array and produce wrong results.  A caller that
+// wants to know whether the state was dry (a non-positive or NaN depth at
+// a wave-speed point, or a projection matrix that is not positive
+// definite) passes a device word of its own, which the kernels OR their
+// flags into.
+//
+// The array's device address is looked up once per device and cached.  A
+// cudaDeviceReset() unloads the library's device image, so the cached
+// address no longer belongs to it: a process that resets a device must not
+// call dg_rhs_noalloc on that device afterwards.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -63,7 +72,7 @@ size_t round_up(size_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
 
 template <class Real>
 dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d_in, void* d_out,
-              cudaStream_t s) {
+              unsigned* d_flags, cudaStream_t s) {
   const int P = cfg->p;
   const int K = (P + 1) * (P + 2) / 2, P1 = P + 1, NREC = 6 * P1 + 1;
   // bathymetry space P^max(p,1): basis size, edge modes, gradient basis
@@ -87,8 +96,10 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   cudaError_t e = scratch_for_current_device(&base);
   if (e != cudaSuccess) return DG_ERR_CUDA;
   unsigned char* b = static_cast<unsigned char*>(base);
-  unsigned* err = reinterpret_cast<unsigned*>(b + o_err);
-  if (cudaMemsetAsync(err, 0, sizeof(unsigned), s) != cudaSuccess) return DG_ERR_CUDA;
+  // the kernels OR their flags into the caller's word, else into the
+  // array's own word (cleared per call, never read back)
+  unsigned* err = d_flags ? d_flags : reinterpret_cast<unsigned*>(b + o_err);
+  if (!d_flags && cudaMemsetAsync(err, 0, sizeof(unsigned), s) != cudaSuccess) return DG_ERR_CUDA;
 
   const Mesh m = make_mesh(cfg->nx, cfg->ny, cfg->x0, cfg->y0, cfg->Lx, cfg->Ly, cfg->bc == DG_BC_PERIODIC);
   const double hx = m.hx, hy = m.hy;
@@ -143,7 +154,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
 }  // namespace
 
 extern "C" dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_state_in,
-                                    void* d_rhs_out, void* stream) {
+                                    void* d_rhs_out, unsigned* d_flags, void* stream) {
   if (!cfg || !d_hb || !d_state_in || !d_rhs_out || d_state_in == d_rhs_out) return DG_ERR_ARG;
   if (cfg->nx < 1 || cfg->ny < 1 || cfg->p < 0 || cfg->p > 4 || !(cfg->Lx > 0.0) || !(cfg->Ly > 0.0) ||
       !(cfg->g > 0.0) || cfg->vertex_xy || cfg->bc < 0 || cfg->bc > 1 || cfg->precision < 0 ||
@@ -159,6 +170,6 @@ extern "C" dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, cons
   if (2.0 * (double)cfg->nx * (double)cfg->ny > 1.0e8) return DG_ERR_ARG;
   const int arith = arith_of(cfg->precision, cfg->proj_precision);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (arith == ARITH_FP64) return run<double>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, s);
-  return run<float>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, s);
+  if (arith == ARITH_FP64) return run<double>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, d_flags, s);
+  return run<float>(cfg, arith, (const double*)d_hb, d_state_in, d_rhs_out, d_flags, s);
 }

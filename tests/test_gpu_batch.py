@@ -54,7 +54,7 @@ def test_batch_equals_single_contexts(precision, proj):
         t = B.dg_run(ctx, steps)
         ref.append((B.dg_get_state(ctx, E, K), t))
         B.dg_destroy(ctx)
-    b = B.dg_batch_init([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
+    b = B.dg_batch_init_device([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
                         [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
     try:
         assert B.dg_batch_dofs(b) == sum(3 * K * E for _, _, E, K in inst)
@@ -74,8 +74,8 @@ def test_batch_set_state_resumes_bit_exactly():
     inst = [_instance(k, *s, "fp32") for k, s in enumerate(SPECS)]
     args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
             [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
-    b1 = B.dg_batch_init(*args)
-    b2 = B.dg_batch_init(*args)
+    b1 = B.dg_batch_init_device(*args)
+    b2 = B.dg_batch_init_device(*args)
     try:
         t5 = B.dg_batch_run(b1, 5)
         for i, (_, _, E, K) in enumerate(inst):
@@ -95,8 +95,8 @@ def test_batch_autotune_keeps_state():
     inst = [_instance(k, *s, "fp32") for k, s in enumerate(SPECS)]
     args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
             [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
-    b1 = B.dg_batch_init(*args)
-    b2 = B.dg_batch_init(*args)
+    b1 = B.dg_batch_init_device(*args)
+    b2 = B.dg_batch_init_device(*args)
     try:
         t1 = B.dg_batch_run(b1, 5)
         blk, ms = B.dg_batch_autotune(b2, 2)
@@ -127,7 +127,7 @@ def test_batch_instance_matches_oracle(oracle_mod):
     cfg = B.make_config(nx, ny, p, bc=bc, precision="fp64", rk_order=3, cfl=0.25)
     dev = [torch.tensor(a.T.copy(), dtype=torch.float64, device="cuda").contiguous() for a in (hb, xi, U, V)]
     other = _instance(0, *SPECS[0], "fp64")
-    b = B.dg_batch_init([other[0], cfg], [other[1][0], dev[0]], [other[1][1], dev[1]],
+    b = B.dg_batch_init_device([other[0], cfg], [other[1][0], dev[0]], [other[1][1], dev[1]],
                         [other[1][2], dev[2]], [other[1][3], dev[3]])
     try:
         t = B.dg_batch_run(b, 20)
@@ -137,3 +137,26 @@ def test_batch_instance_matches_oracle(oracle_mod):
     assert abs(t[1] - tr) <= 1e-13 * tr
     for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr)):
         assert np.linalg.norm(g_ - r_) <= 1e-12 * np.linalg.norm(r_)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_batch_host_and_device_forms_identical(precision):
+    """dg_batch_init from host FP64 AoS arrays (the §8(b) form) and
+    dg_batch_init_device from device SoA arrays build the same batch: after
+    10 steps every instance's state and time agree bit for bit"""
+    inst = [_instance(k, *s, precision) for k, s in enumerate(SPECS)]
+    cfgs = [c for c, *_ in inst]
+    dev = [[f[k] for _, f, _, _ in inst] for k in range(4)]
+    host = [[f[k].t().contiguous().cpu().numpy() for _, f, _, _ in inst] for k in range(4)]
+    b1 = B.dg_batch_init_device(cfgs, *dev)
+    b2 = B.dg_batch_init(cfgs, *host)
+    try:
+        t1 = B.dg_batch_run(b1, 10)
+        t2 = B.dg_batch_run(b2, 10)
+        assert np.array_equal(t1, t2)
+        for i, (_, _, E, K) in enumerate(inst):
+            for a, r in zip(B.dg_batch_get_state(b2, i, E, K), B.dg_batch_get_state(b1, i, E, K)):
+                assert np.array_equal(a, r)
+    finally:
+        B.dg_batch_destroy(b1)
+        B.dg_batch_destroy(b2)

@@ -143,7 +143,7 @@ def test_ensemble_batch_step_sampled(oracle_mod, proj):
             arrs = (hbk, z, z, z)
         for j in range(4):
             fields[j].append(torch.from_numpy(np.ascontiguousarray(arrs[j].T)).cuda())
-    b = B.dg_batch_init(cfgs, *fields)
+    b = B.dg_batch_init_device(cfgs, *fields)
     del fields
     try:
         block, _ = B.dg_batch_autotune(b, 1)

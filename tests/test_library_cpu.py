@@ -96,15 +96,47 @@ def test_batch_rejects_mixed_or_unsupported_without_gpu(lib):
     c = B.make_config(4, 4, 4)
     one = [1, 1]
     with pytest.raises(B.DGError) as ei:
-        B.dg_batch_init([a, b], one, one, one, one)
+        B.dg_batch_init_device([a, b], one, one, one, one)
     assert ei.value.status == B.DG_ERR_ARG
     for unsupported in (c, B.make_config(4, 4, 0)):      # the batched kernel holds p = 1..3
         with pytest.raises(B.DGError) as ei:
-            B.dg_batch_init([unsupported], [1], [1], [1], [1])
+            B.dg_batch_init_device([unsupported], [1], [1], [1], [1])
         assert ei.value.status == B.DG_ERR_UNSUPPORTED
     with pytest.raises(B.DGError) as ei:
-        B.dg_batch_init([], [], [], [], [])
+        B.dg_batch_init_device([], [], [], [], [])
     assert ei.value.status == B.DG_ERR_ARG
+
+
+def test_batch_host_form_validates_before_any_gpu_work(lib):
+    """dg_batch_init (host FP64 AoS arrays, the §8(b) form) applies the same
+    checks as the device form before touching any array or the GPU"""
+    from paper_1904_08684_gb300 import binding as B
+    L = B.load()
+    dp = ctypes.POINTER(ctypes.c_double)
+    fake = ctypes.cast(ctypes.c_void_p(0x1000), dp)          # never dereferenced
+
+    def call(cfgs, ptrs=None, n=None):
+        n = len(cfgs) if n is None else n
+        carr = (B.dg_config * max(1, len(cfgs)))(*cfgs)
+        arrs = []
+        for _ in range(4):
+            a = (dp * max(1, len(cfgs)))()
+            for k in range(len(cfgs)):
+                a[k] = fake if ptrs is None else ptrs[k]
+            arrs.append(a)
+        h = ctypes.c_void_p()
+        return L.dg_batch_init(n, carr, *arrs, None, ctypes.byref(h)), h
+    a = B.make_config(4, 4, 2, precision="fp64")
+    b = B.make_config(4, 4, 1, precision="fp32")
+    assert call([a, b])[0] == B.DG_ERR_ARG                   # mixed precisions
+    assert call([B.make_config(4, 4, 4)])[0] == B.DG_ERR_UNSUPPORTED
+    assert call([B.make_config(4, 4, 0)])[0] == B.DG_ERR_UNSUPPORTED
+    assert call([B.make_config(4, 4, 1, bc="dirichlet", forcing=1)])[0] == B.DG_ERR_UNSUPPORTED
+    assert call([a], n=0)[0] == B.DG_ERR_ARG
+    st, h = call([a], ptrs=[ctypes.cast(None, dp)])             # NULL field array
+    assert st == B.DG_ERR_ARG and not h.value
+    h = ctypes.c_void_p()
+    assert L.dg_batch_init(1, ctypes.byref(a), None, None, None, None, None, ctypes.byref(h)) == B.DG_ERR_ARG
 
 
 def test_plain_c_program_uses_the_abi(lib, tmp_path):
@@ -141,11 +173,11 @@ def test_noalloc_rhs_rejects_before_any_gpu_work(lib, bad, status):
     kw.update(bad)
     cfg = B.make_config(**kw)
     fake = [ctypes.c_void_p(0x1000 * (k + 1)) for k in range(3)]   # never dereferenced
-    got = B.load().dg_rhs_noalloc(ctypes.byref(cfg), fake[0], fake[1], fake[2], None)
+    got = B.load().dg_rhs_noalloc(ctypes.byref(cfg), fake[0], fake[1], fake[2], None, None)
     assert got == getattr(B, "DG_ERR_" + status)
     # the same pointer as input and output is refused
     ok_cfg = B.make_config(4, 4, 1)
-    assert B.load().dg_rhs_noalloc(ctypes.byref(ok_cfg), fake[0], fake[1], fake[1], None) == B.DG_ERR_ARG
+    assert B.load().dg_rhs_noalloc(ctypes.byref(ok_cfg), fake[0], fake[1], fake[1], None, None) == B.DG_ERR_ARG
 
 
 def test_null_handles_are_rejected(lib):

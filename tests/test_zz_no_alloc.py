@@ -2,9 +2,11 @@
 
 Callers that cannot call cudaMalloc (graph capture in progress, fixed device
 budgets) use dg_rhs_noalloc, which keeps its intermediates in a fixed array
-inside the library.  This file is collected last on purpose: if it fails, a
-run that stops at the first failure has already run every other test.  It
-must pass both alone in a fresh process and after the other tests.
+inside the library.  It runs the same kernels as dg_rhs on the same inputs,
+so the two results are compared bit for bit, on two calls in a row.  This
+file is collected last on purpose: if it fails, a run that stops at the
+first failure has already run every other test.  It must pass both alone in
+a fresh process and after the other tests.
 """
 import numpy as np
 import pytest
@@ -17,15 +19,16 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def _fields(wl, seed):
+def _fields(wl, seed, depth_shift=0.0):
     """seeded smooth fields sampled at the library's set-up nodes and
-    projected with dg_project (device FP64 SoA (K, E))"""
+    projected with dg_project (device FP64 SoA (K, E)); depth_shift is
+    added to the bathymetry"""
     cfg = B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc)
     Q, E, K = B.dg_proj_num_nodes(wl.p), wl.E, wl.K
     xy = torch.empty((2, Q, E), dtype=torch.float64, device="cuda")
     B.dg_proj_nodes(cfg, xy)
     r = I.uniform(seed, 4)
-    fields = [wl.hb, I.gaussian_sum([0.05 + 0.05 * r[0]], [0.08], [r[1]], [r[2]]),
+    fields = [lambda x, y: wl.hb(x, y) + depth_shift, I.gaussian_sum([0.05 + 0.05 * r[0]], [0.08], [r[1]], [r[2]]),
               lambda x, y: 0.2 + 0.1 * torch.sin(2 * np.pi * (x + r[3])),
               lambda x, y: -0.1 + 0.05 * torch.cos(2 * np.pi * y)]
     out = []
@@ -45,17 +48,19 @@ def _fields(wl, seed):
     return out
 
 
-@pytest.mark.parametrize("precision,p,proj", [("fp64", 2, "fp64"), ("fp64", 3, "fp64"), ("fp32", 3, "fp64"),
-                                              ("fp64", 0, "fp64"), ("fp32", 3, "mixed"), ("fp32", 2, "df64")])
-def test_noalloc_rhs_equals_dg_rhs_twice(precision, p, proj):
+@pytest.mark.parametrize("precision,p,proj,bc", [
+    ("fp64", 2, "fp64", "periodic"), ("fp64", 3, "fp64", "reflective"), ("fp32", 3, "fp64", "periodic"),
+    ("fp64", 0, "fp64", "reflective"), ("fp64", 1, "fp64", "periodic"), ("fp32", 4, "fp64", "reflective"),
+    ("fp32", 3, "mixed", "periodic"), ("fp32", 2, "df64", "reflective"), ("fp32", 1, "fp32", "periodic")])
+def test_noalloc_rhs_equals_dg_rhs_twice(precision, p, proj, bc):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    wl = I.waves_p2_512(n=37, p=p, ngauss=2)
-    wl.ny = 29                                   # 2146 triangles, ragged last block
-    cfg = B.make_config(wl.nx, wl.ny, p, bc="periodic", precision=precision, rk_order=3, cfl=0.2,
+    wl = I.waves_p2_512(n=37 if p < 4 else 21, p=p, ngauss=2)
+    wl.ny = 29 if p < 4 else 17                  # ragged last block
+    wl.bc = bc
+    cfg = B.make_config(wl.nx, wl.ny, p, bc=bc, precision=precision, rk_order=3, cfl=0.2,
                         proj_precision=proj)
     dt = torch.float64 if precision == "fp64" else torch.float32
-    tol = 1e-13 if precision == "fp64" else 1e-5
     refs, inputs = [], []
     for seed in (11, 12):                        # two different inputs
         hb, xi, U, V = _fields(wl, seed)
@@ -70,16 +75,38 @@ def test_noalloc_rhs_equals_dg_rhs_twice(precision, p, proj):
         refs.append(ref)
         inputs.append((hb, state))
     outs = []
+    flags = torch.zeros(1, dtype=torch.int32, device="cuda")
     for hb, state in inputs:                     # two calls in a row
         out = torch.full_like(state, float("nan"))
-        B.dg_rhs_noalloc(cfg, hb, state, out)
+        B.dg_rhs_noalloc(cfg, hb, state, out, d_flags=flags)
         outs.append(out)
     torch.cuda.synchronize()
+    assert int(flags.item()) == 0
     for call, (o, r) in enumerate(zip(outs, refs)):
-        o = o.double().cpu().numpy()
-        r = r.double().cpu().numpy()
+        o = o.cpu().numpy()
+        r = r.cpu().numpy()
         assert np.isfinite(o).all()
-        assert np.abs(o - r).max() <= tol * np.abs(r).max(), (call, np.abs(o - r).max())
+        # the same kernels on the same inputs: identical bits
+        assert np.array_equal(o, r), (call, np.abs(o - r).max())
+
+
+def test_noalloc_reports_a_dry_state_through_the_flag_word():
+    """a bathymetry lowered below the surface (H <= 0 everywhere) sets
+    DG_FLAG_DRY in the caller's word; without a word the call still returns
+    DG_OK (nothing is read back); a wet state leaves the word at zero"""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    wl = I.waves_p2_512(n=9, p=2, ngauss=1)
+    cfg = B.make_config(wl.nx, wl.ny, 2, bc="periodic", precision="fp64")
+    for shift, want in ((-40.0, B.DG_FLAG_DRY), (0.0, 0)):
+        hb, xi, U, V = _fields(wl, 5, depth_shift=shift)
+        state = torch.stack([xi, U, V]).contiguous()
+        out = torch.empty_like(state)
+        flags = torch.zeros(1, dtype=torch.int32, device="cuda")
+        B.dg_rhs_noalloc(cfg, hb, state, out, d_flags=flags)
+        B.dg_rhs_noalloc(cfg, hb, state, out)
+        torch.cuda.synchronize()
+        assert int(flags.item()) & B.DG_FLAG_DRY == want
 
 
 def test_noalloc_rejects_oversized_mesh():
