@@ -3,18 +3,25 @@
 water solver (arXiv:1904.08684) on one GB300, through the libdgswe C-ABI.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
-                    [--impl ours|reference] [--no-cpu-baseline]
+                    [--proj fp64|fp32|df64|mixed] [--impl ours|reference]
+                    [--no-cpu-baseline] [--no-fp64-plain]
 
-Default workload: waves-p2-512 (512 x 512 quads -> 524,288 triangles, p = 2,
-periodic, h_b = 10 + 2 sin(2 pi x) cos(2 pi y), 8 seeded Gaussians, q = 0,
-SSP-RK3, CFL 0.2, FP64).  A step is one SSP-RK3 time step (3 stage-kernel
-launches, CUDA-graph captured); the metric counts 3 K E updated coefficients
-per stage.  The inputs are synthetic (seeded), projected on the device by the
-library's own set-up projection.
+Default workload: ensemble-256, the batched FP32 form of the headline metric:
+256 seeded independent instances (nx, ny uniform in {64..384}, p uniform in
+{1, 2, 3}, periodic, smooth bathymetry of depth 5-20 m, one Gaussian hump
+each, SSP-RK3, per-instance CFL step), FP32 state and contractions with the
+mixed velocity solve (FP32 factors refined once with an FP64 residual), one
+persistent launch per RK stage, each step one CUDA graph.  Beside it, in the
+same JSON line, "fp64_plain" holds the plain FP64 path measured on
+waves-p2-512 (512 x 512 quads -> 524,288 triangles, p = 2, periodic, h_b = 10
++ 2 sin(2 pi x) cos(2 pi y), 8 seeded Gaussians, q = 0, SSP-RK3, CFL 0.2), and
+"speedup_vs_fp64_plain" the ratio of the two.  The metric counts 3 K E
+updated coefficients per stage.  Inputs are synthetic (seeded), projected on
+the device by the library's own set-up projection.
 
-N > 1 (torchrun): every rank runs an independent replica of the workload
-(the single-instance path has no domain decomposition); value = all ranks'
-DOF-updates / the slowest rank's time.
+N > 1 (torchrun): the ensemble's independent instances are split across the
+ranks (no data-path collective); single-instance workloads run as replicas.
+value = all ranks' DOF-updates / the slowest rank's time.
 
 --impl reference times the FP64 CPU oracle (the test reference) on the host
 cores, on a bounded sample of the same workload.
@@ -63,36 +70,54 @@ FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 2 * 152 * 128 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x max clock
 
 
-def _roofline(parts, precision, proj, launch_s, traffic):
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _hbm_peak():
+    """measured copy bandwidth (GB/s) and where it comes from"""
+    v = _peaks().get("hbm_gbs")
+    if v:
+        return float(v), "of measured (MEASURED_PEAKS.json hbm_gbs)"
+    return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s, no MEASURED_PEAKS.json on this box)"
+
+
+def _roofline(parts, precision, proj, launch_s, traffic, rk_order):
     """Roofline of the stage kernel.  parts: [(p, E)] of the instances of one
-    launch; launch_s: seconds per stage launch.  Algorithmic flops per
-    element and stage: 2 x the FMA counts of flops.ALGORITHMIC_FMA (velocity solve,
-    rest).  FP64 path: all flops against the FP64 rate; FP32 state with FP64
-    solve: the solve's flops against the FP64 rate (the pipe that binds),
-    with the FP32 share beside it; FP32 state with a double-float or FP32
-    solve: all flops against the FP32 rate."""
+    launch; launch_s: seconds per stage launch (the step's CUDA-event time /
+    its stage count).  Algorithmic flops per element and stage: 2 x the FMA
+    counts of flops.ALGORITHMIC_FMA (velocity solve, rest).  FP64 path: all
+    flops against the FP64 rate; FP32 state with the FP64 solve: the solve's
+    flops against the FP64 rate (the pipe that binds), with the FP32 share
+    beside it; FP32 state with a double-float, mixed or FP32 solve: all flops
+    against the FP32 rate.  The HBM fraction uses the algorithmic bytes of
+    flops.stage_bytes_avg (state, RK base from the second stage on,
+    bathymetry in; state out) over the stages of one step."""
     from paper_1904_08684_gb300 import flops as FL
     fsolve = sum(2 * FL.ALGORITHMIC_FMA[p][0] * E for p, E in parts)
     frest = sum(2 * FL.ALGORITHMIC_FMA[p][1] * E for p, E in parts)
     word = 8 if precision == "fp64" else 4
-    alg_bytes = sum(FL.stage_bytes(p, word) * E for p, E in parts)
-    hbm_peak = _peaks().get("hbm_gbs")
-    fp64_src = "FP64 1.25 TFLOP/s nominal (recipe table)"
-    fp32_src = "FP32 152 SM x 128 lanes x 2 x 2.07 GHz"
+    alg_bytes = sum(FL.stage_bytes_avg(p, word, rk_order) * E for p, E in parts)
+    hbm_peak, hbm_src = _hbm_peak()
+    fp64_src = "FP64 1.25 TFLOP/s nominal (recipe table; a probe measured 1.17-1.20)"
+    fp32_src = "FP32 152 SM x 128 lanes x 2 x 2.07 GHz (nominal; a probe measured 73)"
     if precision == "fp64":
-        ach, peak, src, what = (fsolve + frest) / launch_s / 1e12, FP64_PEAK_TFLOPS, fp64_src, "all flops (FP64)"
+        ach, peak, src, what, pipe = ((fsolve + frest) / launch_s / 1e12, FP64_PEAK_TFLOPS, fp64_src,
+                                      "all flops (FP64)", "fp64")
     elif proj == "fp64":
-        ach, peak, src, what = (fsolve / launch_s / 1e12, FP64_PEAK_TFLOPS, fp64_src,
-                                "FP64 flops of the velocity solve")
+        ach, peak, src, what, pipe = (fsolve / launch_s / 1e12, FP64_PEAK_TFLOPS, fp64_src,
+                                      "FP64 flops of the velocity solve", "fp64")
     else:
-        ach, peak, src, what = ((fsolve + frest) / launch_s / 1e12, FP32_PEAK_TFLOPS, fp32_src,
-                                "all flops on the FP32 pipe (the %s solve counted at its algorithmic flops)" % proj)
-    roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+        ach, peak, src, what, pipe = ((fsolve + frest) / launch_s / 1e12, FP32_PEAK_TFLOPS, fp32_src,
+                                      "all flops on the FP32 pipe (the %s solve counted at its algorithmic flops)"
+                                      % proj, "fp32")
+    hbm_ach = alg_bytes / launch_s / 1e9
+    roof = {"bound": "alu", "pipe": pipe, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": traffic, "counted": what, "peak_source": src,
             "flops_per_launch": fsolve + frest,
             "hbm_algorithmic_bytes_per_launch": alg_bytes,
-            "hbm_achieved_gbs": alg_bytes / launch_s / 1e9,
-            "hbm_frac_of_measured": (alg_bytes / launch_s / 1e9) / hbm_peak if hbm_peak else None}
+            "hbm_achieved_gbs": hbm_ach, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+            "hbm_frac": hbm_ach / hbm_peak,
+            "traffic_over_algorithmic": (traffic / alg_bytes) if traffic else None}
     if precision != "fp64" and proj == "fp64":
         roof["fp32_achieved_tflops"] = frest / launch_s / 1e12
         roof["fp32_frac"] = frest / launch_s / 1e12 / FP32_PEAK_TFLOPS
@@ -245,10 +270,6 @@ def run_batch(args, wls):
     n_total = len(wls)
     if world > 1:
         wls = [wls[i] for i in shard_instances(n_total, world, rank)]
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.load()
     stream = torch.cuda.current_stream()
     cfgs, fields = [], [[], [], [], []]
@@ -301,7 +322,8 @@ def run_batch(args, wls):
         B.dg_batch_destroy(b)
     launch_s = step_ms * 1e-3 / S
     roof = _roofline([(wl.p, wl.E) for wl in wls], wls[0].precision, args.proj, launch_s,
-                     _measured_traffic("ensemble-256-" + wls[0].precision + "-" + args.proj, FL.source_hash()))
+                     _measured_traffic("ensemble-256-" + wls[0].precision + "-" + args.proj, FL.source_hash()),
+                     S)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
            "scaling": "strong", "vs_baseline": None,
@@ -326,23 +348,18 @@ def run_batch(args, wls):
         out["cpu_baseline"] = {"value": sum(pp["value"] for pp in parts) / len(parts), "unit": UNIT,
                                "cores": parts[0]["cores"], "kind": "oracle",
                                "sample": "; ".join(pp["sample"] for pp in parts) + " (mean of the p classes)"}
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(out))
+    return out
 
 
-def run_ours(args):
+def run_ours(args, workload=None, proj=None):
     import torch
     from paper_1904_08684_gb300 import binding as B
     from paper_1904_08684_gb300 import flops as FL
     world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.load()
-    wl = WORKLOADS[args.workload]()
+    wl = WORKLOADS[workload or args.workload]()
+    if proj is not None:
+        args = argparse.Namespace(**dict(vars(args), proj=proj))
     cfg = _cfg_of(B, wl, args)
     stream = torch.cuda.current_stream()
     hb, xi, qx, qy = _setup_device_inputs(B, torch, wl, cfg, stream)
@@ -387,7 +404,7 @@ def run_ours(args):
     launch_s = step_ms * 1e-3 / S
     traffic_key = wl.name if wl.precision == "fp64" else wl.name + "-" + args.proj
     roof = _roofline([(wl.p, wl.E)], wl.precision, args.proj, launch_s,
-                     _measured_traffic(traffic_key, FL.source_hash()))
+                     _measured_traffic(traffic_key, FL.source_hash()), S)
     e2e_val = dof_stage * S / e2e_s
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -406,10 +423,7 @@ def run_ours(args):
            "diagnostics": {"mass": mass, "energy": energy}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
-    if world > 1:
-        torch.distributed.destroy_process_group()
-    if rank == 0:
-        print(json.dumps(out))
+    return out
 
 
 def _oracle_sample(wl):
@@ -486,10 +500,11 @@ def run_reference(args):
     sample = "oracle RHS (one RK stage) of 1/16 of the elements of %s, %d evaluations in %.1f s" % (
         ", ".join(w.name for w in wls), reps, el)
     # n_gpus: the launch's N (the oracle itself runs on rank 0's host cores)
+    ens = args.workload.startswith("ensemble")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "device": "host CPU cores (FP64 oracle)",
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "higher_is_better": True, "scaling": "strong" if ens else "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded SplitMix64 fields)",
            "config": {"workload": args.workload, "elements": wl.E, "p": wl.p, "K": wl.K,
                       "rk_stages": wl.rk_order, "precision": "fp64", "bc": wl.bc},
@@ -505,23 +520,46 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="waves-p2-512", choices=sorted(WORKLOADS))
-    ap.add_argument("--proj", default="fp64", choices=["fp64", "fp32", "df64", "mixed"],
-                    help="velocity-solve arithmetic of the FP32 state path")
+    ap.add_argument("--workload", default="ensemble-256", choices=sorted(WORKLOADS))
+    ap.add_argument("--proj", default=None, choices=["fp64", "fp32", "df64", "mixed"],
+                    help="velocity-solve arithmetic of the FP32 state path (default: mixed for "
+                         "ensemble-256, fp64 otherwise)")
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = library default)")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=0, help="ensemble: use only the first N instances")
+    ap.add_argument("--no-fp64-plain", action="store_true",
+                    help="ensemble: skip the nested plain FP64 measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)      # timing rule: at least 3 untimed steps
+    if args.proj is None:
+        args.proj = "mixed" if args.workload == "ensemble-256" else "fp64"
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload.startswith("ensemble"):
+        return
+    import torch
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.workload.startswith("ensemble"):
         wls = WORKLOADS[args.workload]()
-        run_batch(args, wls[:args.instances] if args.instances > 0 else wls)
+        out = run_batch(args, wls[:args.instances] if args.instances > 0 else wls)
+        if not args.no_fp64_plain:
+            # the plain FP64 path on waves-p2-512, same launch, same box
+            plain_args = argparse.Namespace(**dict(vars(args), no_cpu_baseline=True))
+            plain = run_ours(plain_args, workload="waves-p2-512", proj="fp64")
+            keep = ("value", "unit", "ms_per_step", "dtype", "config", "gpu_launches", "roofline", "e2e", "clocks")
+            out["fp64_plain"] = {k: plain[k] for k in keep}
+            out["speedup_vs_fp64_plain"] = out["value"] / plain["value"]
     else:
-        run_ours(args)
+        out = run_ours(args)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
 
 
 if __name__ == "__main__":

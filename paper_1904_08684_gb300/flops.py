@@ -123,6 +123,13 @@ def stage_bytes(p, word_bytes, with_base=True):
     return words * word_bytes
 
 
+def stage_bytes_avg(p, word_bytes, rk_order):
+    """algorithmic HBM bytes per element and stage, averaged over the stages
+    of one SSP-RK step (the first stage reads no RK base state)"""
+    S = rk_order
+    return (stage_bytes(p, word_bytes, False) + (S - 1) * stage_bytes(p, word_bytes, True)) / S
+
+
 def stage_bytes_kernel(p, word_bytes, with_base=True):
     """bytes per element and stage the stage kernel moves by design (own and
     neighbour side records, volume integrals, static bathymetry fields)"""
