@@ -13,6 +13,8 @@ quickly, so it computes sampled outputs element by element:
   the domain of dependence of the samples (stage s needs the previous stage
   on the samples' neighbours), with the oracle's own CFL time step.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -143,3 +145,42 @@ def test_coefficient_offsets_beyond_2_31():
     finally:
         B.dg_destroy(ctx)
         torch.cuda.empty_cache()
+
+
+GOLDEN_RUN100 = os.path.join(os.path.dirname(__file__), "golden", "waves512_run100.npz")
+
+
+def test_full_size_run_100_steps_matches_stored_oracle_run(oracle_mod):
+    """dg_run(100) of the bench's FP64 workload (512 x 512 quads, p = 2,
+    periodic, SSP-RK3, CFL 0.2, q = 0, graph-launched, 128-thread blocks)
+    against the FP64 oracle's own 100-step run of the whole mesh, stored at
+    ~2000 sampled elements (seams included) by tests/golden/
+    make_waves512_run100.py: relative L2 <= 1e-12 per field, and the same
+    simulation time.  Both start from the oracle's projection of the same
+    seeded fields."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if not os.path.exists(GOLDEN_RUN100):
+        pytest.fail("missing %s (run tests/golden/make_waves512_run100.py)" % GOLDEN_RUN100)
+    ref = np.load(GOLDEN_RUN100)
+    wl = I.waves_p2_512()
+    o = oracle_mod.Oracle(wl.nx, wl.ny, wl.p, bc="periodic", rk_order=3, cfl=wl.cfl)
+    xy = o.proj_nodes()
+    hb = o.project_hb_values(wl.hb(xy[..., 0], xy[..., 1]))
+    xi = o.project_values(wl.xi0(xy[..., 0], xy[..., 1]))
+    del xy
+    z = np.zeros_like(xi)
+    cfg = B.make_config(wl.nx, wl.ny, wl.p, bc="periodic", precision="fp64", rk_order=3, cfl=wl.cfl)
+    ctx = B.dg_init(cfg, hb, xi, z, z)
+    try:
+        t = B.dg_run(ctx, 100)
+        xg, Ug, Vg = B.dg_get_state(ctx, o.E, o.K)
+    finally:
+        B.dg_destroy(ctx)
+    S = ref["elems"]
+    assert abs(t - float(ref["t"])) <= 1e-13 * float(ref["t"])
+    for name, g_ in (("xi", xg), ("U", Ug), ("V", Vg)):
+        r_ = ref[name]
+        rel = np.linalg.norm(g_[S] - r_) / np.linalg.norm(r_)
+        print("100-step %s rel L2 %.2e" % (name, rel))
+        assert rel <= 1e-12, (name, rel)
