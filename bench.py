@@ -249,7 +249,7 @@ def _dtype(precision, proj):
 def _cfg_of(B, wl, args):
     return B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc, precision=wl.precision, rk_order=wl.rk_order,
                          cfl=wl.cfl, dt=wl.dt, g=wl.g, x0=wl.x0, y0=wl.y0, Lx=wl.Lx, Ly=wl.Ly,
-                         proj_precision=args.proj, block_size=args.block)
+                         proj_precision=args.proj, block_size=args.block, tile_shape=args.tile)
 
 
 def shard_instances(n, world, rank):
@@ -284,6 +284,9 @@ def run_batch(args, wls):
     torch.cuda.empty_cache()
     S = wls[0].rk_order
     dofs = B.dg_batch_dofs(b)
+    tiled = wls[0].precision == "fp32" and args.tile >= 0
+    shape_names = {0: "8x8 quads", 1: "16x8 quads", 2: "8x4 quads"}
+    cand_names = [shape_names[k] for k in range(3)] if tiled else ["%d elements" % k for k in (32, 64, 96, 128)]
     try:
         block, tune_ms = B.dg_batch_autotune(b, 2)
         B.dg_batch_run(b, args.warmup)
@@ -334,8 +337,9 @@ def run_batch(args, wls):
                       "elements_this_rank": sum(wl.E for wl in wls),
                       "p_counts": {str(q): sum(1 for wl in wls if wl.p == q) for q in (1, 2, 3)},
                       "dof_per_stage": dofs, "rk_stages": S, "precision": wls[0].precision,
-                      "block": block, "autotune_ms_per_step": {str(bb): float(m) for bb, m in
-                                                               zip((32, 64, 96, 128), tune_ms)},
+                      "kernel_form": "tile-fused" if tiled else "per-element",
+                      "launch_shape": shape_names[block] if tiled else "%d elements per work item" % block,
+                      "autotune_ms_per_step": {nm: float(m) for nm, m in zip(cand_names, tune_ms) if m > 0},
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": ("instances split over %d ranks" % world) if world > 1 else "single GPU"},
            "gpu_launches": S * args.steps, "roofline": roof,   # one persistent launch per stage
@@ -411,6 +415,8 @@ def run_ours(args, workload=None, proj=None):
            "vs_baseline": None, "dtype": _dtype(wl.precision, args.proj),
            "data": "synthetic (seeded SplitMix64 fields, projected on device)",
            "config": {"workload": wl.name, "elements": wl.E, "p": wl.p, "K": wl.K, "rk_stages": S,
+                      "kernel_form": ("tile-fused %s quads" % {0: "8x8", 1: "16x8", 2: "8x4"}[args.tile]
+                                      if wl.precision == "fp32" and args.tile >= 0 else "per-element"),
                       "dof_per_stage": dof_stage, "precision": wl.precision, "bc": wl.bc,
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -525,6 +531,8 @@ def main():
                     help="velocity-solve arithmetic of the FP32 state path (default: mixed for "
                          "ensemble-256, fp64 otherwise)")
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = library default)")
+    ap.add_argument("--tile", type=int, default=0, choices=[-1, 0, 1, 2],
+                    help="FP32 kernel form: tile shape 0 (8x8), 1 (16x8), 2 (8x4) quads, or -1 per-element")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -70,13 +70,15 @@ typedef enum {
 
 typedef enum { DG_BC_PERIODIC = 0, DG_BC_REFLECTIVE = 1, DG_BC_DIRICHLET = 2 } dg_bc;
 typedef enum { DG_PREC_FP64 = 0, DG_PREC_FP32_MIXED = 1 } dg_precision;
-/* Arithmetic of the velocity solve of DG_PREC_FP32_MIXED: FP64 (default);
- * FP32; double-float (pairs of FP32 numbers, ~48 significant bits, on the
- * FP32 units; p <= 3); or MIXED: FP32 LDL^T and solves plus one step of
- * iterative refinement with the residual formed in FP64, which returns the
- * FP64 solution to within FP32 rounding while the FP32 factors hold
- * (elements whose FP32 pivots fail or spread by more than 2^10 take the FP64
- * solve).  DF64 and MIXED: uniform meshes without forcing only. */
+/* Arithmetic of the velocity solve (u = q/H, Eq. (12)) of DG_PREC_FP32_MIXED:
+ * FP64 (default); FP32; double-float (pairs of FP32 numbers, ~48 significant
+ * bits, on the FP32 units; p <= 3); or MIXED: FP32 LDL^T and solves plus one
+ * step of iterative refinement whose residual is accurate to ~48 bits (a
+ * compensated FP32 dot product with the static bathymetry matrix kept as
+ * float pairs), which returns the FP64 solution to within FP32 rounding
+ * while the FP32 factors hold (elements whose FP32 pivots fail or spread by
+ * more than 2^10 take the FP64 solve).  DF64 and MIXED: uniform meshes
+ * without forcing only. */
 typedef enum { DG_PROJ_FP64 = 0, DG_PROJ_FP32 = 1, DG_PROJ_DF64 = 2, DG_PROJ_MIXED = 3 } dg_proj_precision;
 /* §3.1 convergence test of the paper: xi = 2.3 - 0.4 S, U = 0.6 + 0.04 S,
  * V = 0.3 + 0.04 S, S = sin(pi (x + y + 0.2 t) / 600), on the bathymetry
@@ -117,6 +119,15 @@ typedef struct {
                               body force of the §3.1 analytic solution and,
                               with DG_BC_DIRICHLET, uses that solution as the
                               boundary data                                    */
+  int tile_shape;          /* kernel form of the time step for DG_PREC_FP32_MIXED
+                              on uniform meshes without forcing (other
+                              configurations ignore it): 0 (default), 1 or 2 =
+                              tile-fused stages over 8 x 8, 16 x 8 or 8 x 4
+                              quads, intermediates in shared memory; -1 = one
+                              thread per triangle with the intermediates in
+                              HBM.
+                              Both give the same scheme (agreeing to FP32
+                              rounding); dg_rhs always uses the latter       */
 } dg_config;
 
 typedef struct dg_ctx dg_ctx;
@@ -274,8 +285,9 @@ typedef struct dg_batch dg_batch;
  * Eqs. (13)-(14) per instance; batching is not in the paper).  cfgs[i] as
  * for dg_init with p = 1..3, nx, ny >= 2, uniform meshes without forcing
  * (else DG_ERR_UNSUPPORTED).  All instances share precision,
- * proj_precision, rk_order and fixed-vs-CFL time stepping (else
- * DG_ERR_ARG).  hb[i], xi[i], qx[i], qy[i]: HOST FP64 AoS arrays [E_i][K_i]
+ * proj_precision, rk_order, fixed-vs-CFL time stepping and the kernel form
+ * (tile_shape >= 0 or -1; else DG_ERR_ARG); the initial tile shape is
+ * cfgs[0]'s.  hb[i], xi[i], qx[i], qy[i]: HOST FP64 AoS arrays [E_i][K_i]
  * (as for dg_init; caller-owned, copied: each instance is transposed and
  * uploaded through one reused staging buffer).  Synchronises the stream.
  * Errors: DG_ERR_ARG (checked before any CUDA call), DG_ERR_UNSUPPORTED
@@ -310,17 +322,21 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
 dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double* qx, const double* qy, double t);
 
 /* Autotuner of the batched launch (not in the paper; it changes only the
- * launch shape, never the arithmetic): times trial_steps steps with 32, 64,
- * 96 and 128 elements per
- * work item (one thread per element), restoring the state after each, and
- * keeps the fastest; *block_out (may be NULL) receives it and ms_out (NULL or
- * 4 doubles) the ms per step of each.  State and times are unchanged on
- * return.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+ * launch shape, never the arithmetic): times trial_steps steps of each
+ * candidate shape, restoring the state after each, and keeps the fastest.
+ * Candidates: tile-fused batches (FP32, tile_shape >= 0) tiles of 8 x 8,
+ * 16 x 8 and 8 x 4 quads (128, 256, 64 triangles per CTA, shapes 0, 1, 2);
+ * per-element batches 32, 64, 96 and 128 elements per work item (one thread
+ * per element).  *block_out (may be NULL) receives the chosen shape index or
+ * element count and ms_out (NULL or 4 doubles) the ms per step of each
+ * candidate in that order (0 where there is none).  State and times are
+ * unchanged on return.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out);
 
-/* set the elements per work item of the batched launch (not in the paper;
- * 32, 64, 96 or 128; DG_ERR_ARG otherwise); on any error the batch keeps its
- * previous setting.  Synchronises the stream. */
+/* set the launch shape of the batch (not in the paper): a tile shape 0..2
+ * for tile-fused batches, else 32, 64, 96 or 128 elements per work item;
+ * DG_ERR_ARG otherwise.  On any error the batch keeps its previous setting.
+ * Synchronises the stream. */
 dg_status dg_batch_set_block(dg_batch* b, int block);
 
 /* degrees of freedom updated per RK stage: sum over instances of 3 K E (the

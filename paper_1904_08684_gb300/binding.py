@@ -45,12 +45,13 @@ class dg_config(ctypes.Structure):
                 ("bc", ctypes.c_int), ("precision", ctypes.c_int), ("rk_order", ctypes.c_int),
                 ("cfl", ctypes.c_double), ("dt", ctypes.c_double),
                 ("proj_precision", ctypes.c_int), ("block_size", ctypes.c_int),
-                ("tau_bf", ctypes.c_double), ("f_c", ctypes.c_double), ("forcing", ctypes.c_int)]
+                ("tau_bf", ctypes.c_double), ("f_c", ctypes.c_double), ("forcing", ctypes.c_int),
+                ("tile_shape", ctypes.c_int)]
 
 
 def make_config(nx, ny, p, bc="periodic", precision="fp64", rk_order=3, cfl=0.2, dt=0.0, g=9.81,
                 x0=0.0, y0=0.0, Lx=1.0, Ly=1.0, proj_precision="fp64", block_size=0, tau_bf=0.0, f_c=0.0,
-                vertex_xy=None, forcing=0):
+                vertex_xy=None, forcing=0, tile_shape=0):
     vxy = None
     if vertex_xy is not None:
         _keep = np.ascontiguousarray(vertex_xy, dtype=np.float64).ravel()
@@ -60,7 +61,7 @@ def make_config(nx, ny, p, bc="periodic", precision="fp64", rk_order=3, cfl=0.2,
                      PREC[precision] if isinstance(precision, str) else int(precision),
                      rk_order, cfl, dt,
                      PROJ[proj_precision] if isinstance(proj_precision, str) else int(proj_precision), block_size,
-                     float(tau_bf), float(f_c), int(forcing))
+                     float(tau_bf), float(f_c), int(forcing), int(tile_shape))
     if vertex_xy is not None:
         cfg._vertex_keep = _keep   # keep the vertex array alive with the struct
     return cfg

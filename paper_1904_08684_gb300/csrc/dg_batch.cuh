@@ -11,6 +11,7 @@
 #pragma once
 
 #include "dg_kernels.cuh"
+#include "dg_tile.cuh"
 
 namespace dgswe {
 
@@ -26,7 +27,7 @@ struct BatchInst {
   const void* hbt;
   const void* ghb;
   const void* lin;     // FP64 batches: [2][K][K][E], else null
-  const double* ahb;   // mixed-solve batches: [K(K+1)/2][E], else null
+  const float2* ahb;   // mixed-solve batches: [K(K+1)/2][E] float pairs, else null
   double* lam;         // slot s of this instance at lam[s * n_inst]
   double* t;
   int p;
@@ -129,6 +130,107 @@ __global__ void __launch_bounds__(128, (stage_min_blocks<3, Real>())) batch_kern
     if (MODE == MODE_STAGE && a.last && item.start == 0 && threadIdx.x == 0) *d.t += dt;
   }
 }
+
+// Tile-fused form of the batched stage (FP32 state): work items are
+// (instance, tile) pairs, p = 3 items first; the dynamic shared memory is
+// sized for p = 3, the largest order of a batch.  The per-tile work is
+// tile_stage_body, as in the single-instance tile kernel, so results equal
+// those of single contexts with the same tile shape.
+template <class PR, int TX, int TY>
+__global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<3, TX, TY>()))
+    batch_tile_kernel(const BatchArgs a) {
+  extern __shared__ float tile_smem[];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= a.n_items) break;
+    const BatchItem item = a.items[it];
+    const BatchInst& d = a.inst[item.inst];
+    StageParams<float> sp;
+    sp.m = d.m;
+    sp.g = float(d.g);
+    sp.hb = static_cast<const float*>(d.hb);
+    sp.hbt = static_cast<const float*>(d.hbt);
+    sp.ghb = static_cast<const float*>(d.ghb);
+    sp.lin = nullptr;
+    sp.ahb = d.ahb;
+    sp.inv_det = d.inv_det;
+    sp.det = d.det;
+    sp.tau_bf = d.tau_bf;
+    sp.f_c = d.f_c;
+    sp.err = a.err;
+    sp.dt_fixed = d.dt_fixed;
+    sp.cfl_num = d.cfl_num;
+    sp.alpha = a.alpha;
+    sp.beta = a.beta;
+    sp.w = static_cast<const float*>(d.w[a.win]);
+    sp.wout = static_cast<float*>(d.w[a.wout]);
+    sp.w0 = static_cast<const float*>(d.w[0]);
+    sp.vs = sp.rec = nullptr;
+    sp.vs_out = sp.rec_out = sp.rhs_out = nullptr;
+    sp.lam_clear = nullptr;
+    sp.forcing = 0;
+    sp.dirichlet = 0;
+    sp.t_now = nullptr;
+    sp.c_eval = 0.0;
+    sp.vq = nullptr;
+    sp.nqv = 0;
+    sp.eq = nullptr;
+    sp.nqe = 0;
+    sp.lam = d.lam + (long long)a.lc * a.n_inst;
+    const double dt = d.dt_fixed > 0.0 ? d.dt_fixed : d.cfl_num / sp.lam[0];
+    double* lam_target = (a.last && !(d.dt_fixed > 0.0)) ? d.lam + (long long)(1 - a.lc) * a.n_inst : nullptr;
+    sp.lam_next = lam_target;
+    const int tiles_x = (d.m.nx + TX - 1) / TX;
+    double lam_e = 0.0;
+    unsigned err = 0;
+    switch (d.p) {
+      case 1: tile_stage_body<1, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err); break;
+      case 2: tile_stage_body<2, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err); break;
+      default: tile_stage_body<3, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err); break;
+    }
+    if (lam_target) {
+      const double l = block_max(lam_e);
+      if (threadIdx.x == 0) atomic_max_nonneg(lam_target, l);
+    }
+    if (err) atomicOr(a.err, err);
+    if (a.last && item.start == 0 && threadIdx.x == 0) *d.t += dt;
+  }
+}
+
+template <class PR, int TX, int TY>
+cudaError_t batch_tile_launch_shape(int grid, const BatchArgs& a, cudaStream_t s) {
+  auto kern = batch_tile_kernel<PR, TX, TY>;
+  const size_t smem = sizeof(float) * tile_smem_floats<3, TX, TY>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, TileShape<TX, TY>::NT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class PR, int TX, int TY>
+cudaError_t batch_tile_occupancy_shape(int* blocks_per_sm) {
+  auto kern = batch_tile_kernel<PR, TX, TY>;
+  const size_t smem = sizeof(float) * tile_smem_floats<3, TX, TY>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, TileShape<TX, TY>::NT, smem);
+}
+
+// quads per tile side of each shape (kTileShapes entries)
+__host__ __device__ constexpr int tile_tx(int shape) { return shape == 1 ? 16 : 8; }
+__host__ __device__ constexpr int tile_ty(int shape) { return shape == 2 ? 4 : 8; }
+
+#define DGSWE_BATCH_TILE_DECLARE(SUFFIX)                                                               \
+  cudaError_t batch_tile_launch_##SUFFIX(int shape, int grid, const BatchArgs& a, cudaStream_t s);      \
+  cudaError_t batch_tile_occupancy_##SUFFIX(int shape, int* blocks_per_sm);
+DGSWE_BATCH_TILE_DECLARE(fp32p64)
+DGSWE_BATCH_TILE_DECLARE(fp32p32)
+DGSWE_BATCH_TILE_DECLARE(fp32pdf)
+DGSWE_BATCH_TILE_DECLARE(fp32pir)
 
 // Launch and occupancy of one (arithmetic, mode) instantiation; each is
 // compiled separately from dg_batch_inst.cu (build flags select it), and the

@@ -78,7 +78,8 @@ struct dg_batch {
   BatchInst* d_inst = nullptr;
   BatchItem* d_items = nullptr;
   int n_items = 0;
-  int block = 0, grid = 0;
+  int block = 0, grid = 0;     // per-element: elements per item; tiled: tile shape
+  bool tiled = false;           // FP32: tile-fused stage kernels
   int ep = 0, lc = 0;
   bool evaluated = false;
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -88,6 +89,14 @@ struct dg_batch {
 namespace {
 
 cudaError_t launch_batch(const dg_batch* b, int mode, const BatchArgs& a, cudaStream_t s) {
+  if (b->tiled && mode == MODE_STAGE) {
+    switch (b->arith) {
+      case ARITH_FP32_P64: return batch_tile_launch_fp32p64(b->block, b->grid, a, s);
+      case ARITH_FP32_PDF: return batch_tile_launch_fp32pdf(b->block, b->grid, a, s);
+      case ARITH_FP32_PIR: return batch_tile_launch_fp32pir(b->block, b->grid, a, s);
+      default: return batch_tile_launch_fp32p32(b->block, b->grid, a, s);
+    }
+  }
   switch (b->arith) {
     case ARITH_FP64: return batch_launch_fp64(mode, b->grid, b->block, a, s);
     case ARITH_FP32_P64: return batch_launch_fp32p64(mode, b->grid, b->block, a, s);
@@ -111,6 +120,25 @@ BatchArgs base_args(const dg_batch* b) {
 dg_status launch_eval(dg_batch* b, cudaStream_t s) {
   CK(cudaMemsetAsync(b->counters, 0, sizeof(unsigned), s));
   CK(cudaMemsetAsync(b->lam + (size_t)b->lc * b->n, 0, sizeof(double) * b->n, s));
+  if (b->tiled) {
+    // the tile-fused stages evaluate their own input: only the first step's
+    // CFL maximum of every instance is needed
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (int i = 0; i < b->n; ++i) {
+      const HostInst& h = b->inst[i];
+      long long g = (h.E + 255) / 256;
+      if (g > 4LL * sms) g = 4LL * sms;
+      const Mesh m = make_mesh(h.cfg.nx, h.cfg.ny, h.cfg.x0, h.cfg.y0, h.cfg.Lx, h.cfg.Ly,
+                               h.cfg.bc == DG_BC_PERIODIC);
+      wave_speed_kernel<float><<<(unsigned)g, 256, 0, s>>>(m, float(h.cfg.g), h.K, (const float*)((char*)b->w[0] + h.o_state),
+                                                           (const float*)((char*)b->hb + h.o_hb),
+                                                           b->lam + (size_t)b->lc * b->n + i);
+      CK(cudaGetLastError());
+    }
+    return DG_OK;
+  }
   BatchArgs a = base_args(b);
   a.counter = b->counters;
   a.pin = b->ep;
@@ -174,13 +202,22 @@ dg_status get_graph(dg_batch* b, cudaGraphExec_t* out) {
 //
 // The batch changes only once the new list is on the device: on any failure
 // it keeps its previous items, block and graphs.
+//
+// Tiled batches (block = tile shape index): one item per tile of
+// tile_tx x tile_ty quads, in the same order of orders.
 dg_status build_items(dg_batch* b, int block) {
   std::vector<BatchItem> items;
   try {
     for (int p = 3; p >= 1; --p)
       for (int i = 0; i < b->n; ++i) {
         if (b->inst[i].p != p) continue;
-        for (long long s = 0; s < b->inst[i].E; s += block) items.push_back({i, (int)s});
+        if (b->tiled) {
+          const int tx = tile_tx(block), ty = tile_ty(block);
+          const long long nt = (long long)((b->inst[i].cfg.nx + tx - 1) / tx) * ((b->inst[i].cfg.ny + ty - 1) / ty);
+          for (long long k = 0; k < nt; ++k) items.push_back({i, (int)k});
+        } else {
+          for (long long s = 0; s < b->inst[i].E; s += block) items.push_back({i, (int)s});
+        }
       }
   } catch (const std::exception&) {   // no C++ exception crosses the C ABI
     return DG_ERR_OOM;
@@ -188,12 +225,21 @@ dg_status build_items(dg_batch* b, int block) {
   if (items.size() > (size_t)INT_MAX) return DG_ERR_ARG;
   int occ = 0;
   cudaError_t e;
-  switch (b->arith) {
-    case ARITH_FP64: e = batch_occupancy_fp64(block, &occ); break;
-    case ARITH_FP32_P64: e = batch_occupancy_fp32p64(block, &occ); break;
-    case ARITH_FP32_PDF: e = batch_occupancy_fp32pdf(block, &occ); break;
-    case ARITH_FP32_PIR: e = batch_occupancy_fp32pir(block, &occ); break;
-    default: e = batch_occupancy_fp32p32(block, &occ); break;
+  if (b->tiled) {
+    switch (b->arith) {
+      case ARITH_FP32_P64: e = batch_tile_occupancy_fp32p64(block, &occ); break;
+      case ARITH_FP32_PDF: e = batch_tile_occupancy_fp32pdf(block, &occ); break;
+      case ARITH_FP32_PIR: e = batch_tile_occupancy_fp32pir(block, &occ); break;
+      default: e = batch_tile_occupancy_fp32p32(block, &occ); break;
+    }
+  } else {
+    switch (b->arith) {
+      case ARITH_FP64: e = batch_occupancy_fp64(block, &occ); break;
+      case ARITH_FP32_P64: e = batch_occupancy_fp32p64(block, &occ); break;
+      case ARITH_FP32_PDF: e = batch_occupancy_fp32pdf(block, &occ); break;
+      case ARITH_FP32_PIR: e = batch_occupancy_fp32pir(block, &occ); break;
+      default: e = batch_occupancy_fp32p32(block, &occ); break;
+    }
   }
   CK(e);
   int dev = 0, sms = 0;
@@ -249,6 +295,7 @@ dg_status validate_one(const dg_config* c) {
   if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
   if (c->rk_order < 1 || c->rk_order > 3 || c->bc < 0 || c->bc > 2) return DG_ERR_ARG;
   if (c->precision < 0 || c->precision > 1 || c->proj_precision < 0 || c->proj_precision > 3) return DG_ERR_ARG;
+  if (c->tile_shape < -1 || c->tile_shape > 2) return DG_ERR_ARG;
   if (c->bc == DG_BC_DIRICHLET || c->vertex_xy || c->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
   if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
   if (2.0 * c->nx * (double)c->ny > 2.0e9) return DG_ERR_ARG;
@@ -264,7 +311,8 @@ dg_status validate_batch(int n, const dg_config* cfgs, const void* const* hb, co
     if (s != DG_OK) return s;
     if (!hb[i] || !xi[i] || !qx[i] || !qy[i]) return DG_ERR_ARG;
     if (cfgs[i].precision != cfgs[0].precision || cfgs[i].proj_precision != cfgs[0].proj_precision ||
-        cfgs[i].rk_order != cfgs[0].rk_order || (cfgs[i].dt > 0.0) != (cfgs[0].dt > 0.0))
+        cfgs[i].rk_order != cfgs[0].rk_order || (cfgs[i].dt > 0.0) != (cfgs[0].dt > 0.0) ||
+        (cfgs[i].tile_shape >= 0) != (cfgs[0].tile_shape >= 0))
       return DG_ERR_ARG;
   }
   return DG_OK;
@@ -334,6 +382,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
   b->S = cfgs[0].rk_order;
   b->adaptive = !(cfgs[0].dt > 0.0);
   b->stream = (cudaStream_t)stream;
+  b->tiled = b->arith != ARITH_FP64 && cfgs[0].tile_shape >= 0;
   size_t ost = 0, orec = 0, ohb = 0, ohbt = 0, oghb = 0, olin = 0, oahb = 0;
   b->dofs = 0;
   for (int i = 0; i < n; ++i) {
@@ -358,7 +407,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     ohbt += align256((size_t)3 * h.P1 * h.E * b->rsz);
     oghb += align256((size_t)2 * h.K1 * h.E * b->rsz);
     if (b->arith == ARITH_FP64) olin += align256((size_t)2 * h.K * h.K * h.E * b->rsz);
-    if (b->arith == ARITH_FP32_PIR) oahb += align256(sizeof(double) * tri_size(h.K) * h.E);
+    if (b->arith == ARITH_FP32_PIR) oahb += align256(sizeof(float2) * tri_size(h.K) * h.E);
     b->dofs += 3LL * h.K * h.E;
     b->inst.push_back(h);
   }
@@ -371,7 +420,9 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     if (e != cudaSuccess) st = cuda_status(e);
   };
   for (int k = 0; k < 3; ++k) alloc(&b->w[k], ost);
-  for (int k = 0; k < 2; ++k) {
+  // per-element kernels hand volume integrals and side records from one
+  // launch to the next; the tile-fused kernels keep them in shared memory
+  for (int k = 0; k < 2 && !b->tiled; ++k) {
     alloc(&b->vs[k], ost);
     alloc(&b->rec[k], orec);
   }
@@ -420,7 +471,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     d.hbt = (char*)b->hbt + h.o_hbt;
     d.ghb = (char*)b->ghb + h.o_ghb;
     d.lin = b->lin ? (char*)b->lin + h.o_lin : nullptr;
-    d.ahb = b->ahb ? (const double*)((char*)b->ahb + h.o_ahb) : nullptr;
+    d.ahb = b->ahb ? (const float2*)((char*)b->ahb + h.o_ahb) : nullptr;
     d.lam = b->lam + i;
     d.t = b->t + i;
     d.p = h.p;
@@ -439,7 +490,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
       case ARITH_FP32_PDF: e = static_fp32pdf(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
       case ARITH_FP32_PIR:
         e = static_fp32pir(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s);
-        if (e == cudaSuccess) e = static_ahb(h.p, d.m, hbi, (double*)d.ahb, s);
+        if (e == cudaSuccess) e = static_ahb(h.p, d.m, hbi, (float2*)d.ahb, s);
         break;
       default: e = static_fp32p32(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
     }
@@ -451,7 +502,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     free_batch(b);
     return st != DG_OK ? st : cuda_status(e);
   }
-  if ((st = build_items(b, 128)) != DG_OK) {
+  if ((st = build_items(b, b->tiled ? (cfgs[0].tile_shape > 0 ? cfgs[0].tile_shape : 0) : 128)) != DG_OK) {
     free_batch(b);
     return st;
   }
@@ -497,7 +548,8 @@ void dg_batch_destroy(dg_batch* b) {
 long long dg_batch_dofs(const dg_batch* b) { return b ? b->dofs : 0; }
 
 dg_status dg_batch_set_block(dg_batch* b, int block) {
-  if (!b || block < 32 || block > 128 || block % 32) return DG_ERR_ARG;
+  if (!b) return DG_ERR_ARG;
+  if (b->tiled ? (block < 0 || block >= kTileShapes) : (block < 32 || block > 128 || block % 32)) return DG_ERR_ARG;
   CK(cudaStreamSynchronize(b->stream));
   return build_items(b, block);
 }
@@ -588,10 +640,12 @@ dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double*
   return DG_OK;
 }
 
-// Autotuner: times trial_steps steps at every candidate block size (elements
-// per work item) on the batch's own state, restoring the state after each,
-// and keeps the fastest.  ms_out[4] receives the time per step of 32, 64, 96
-// and 128.
+// Autotuner: times trial_steps steps at every candidate launch shape on the
+// batch's own state, restoring the state after each, and keeps the fastest.
+// Per-element kernels: 32, 64, 96, 128 elements per work item; tile-fused
+// kernels: tiles of 8 x 8, 16 x 8 and 8 x 4 quads (128, 256 and 64 owned
+// triangles per CTA).  ms_out[4] receives the time per step of each
+// candidate in that order (0 where there is none).
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out) {
   dgswe::NvtxRange nvtx_range("dg_batch_autotune");
   if (!b || trial_steps < 1) return DG_ERR_ARG;
@@ -601,7 +655,10 @@ dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double
   double* save_t = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   const int ep0 = b->ep, lc0 = b->lc;
-  const int cand[4] = {32, 64, 96, 128};
+  const int cand_el[4] = {32, 64, 96, 128}, cand_tile[4] = {0, 1, 2, -1};
+  const int* cand = b->tiled ? cand_tile : cand_el;
+  if (ms_out)
+    for (int c = 0; c < 4; ++c) ms_out[c] = 0.0;
   double best = 1e300;
   int best_block = b->block;
   dg_status s = DG_OK;
@@ -613,6 +670,7 @@ dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   for (int c = 0; c < 4 && ce == cudaSuccess && s == DG_OK; ++c) {
     const int block = cand[c];
+    if (block < 0) break;
     if ((s = build_items(b, block)) != DG_OK) break;
     b->evaluated = false;
     b->ep = ep0;

@@ -5,6 +5,7 @@
 // (dg_batch_inst.cu).  Orders outside 0..4 return cudaErrorInvalidValue.
 #include "dg_batch.cuh"
 #include "dg_launch.cuh"
+#include "dg_tile.cuh"
 
 namespace dgswe {
 
@@ -28,6 +29,23 @@ DGSWE_DISPATCH(fp32p64_gen)
 DGSWE_DISPATCH(fp32p32_gen)
 DGSWE_DISPATCH(fp32pdf)
 DGSWE_DISPATCH(fp32pir)
+
+#define DGSWE_TILE_DISPATCH(SUFFIX)                                                                   \
+  cudaError_t tile_##SUFFIX(int p, int shape, const StageParams<float>& sp, cudaStream_t s) {          \
+    switch (p) {                                                                                      \
+      case 0: return tile_##SUFFIX##_p0(shape, sp, s);                                                \
+      case 1: return tile_##SUFFIX##_p1(shape, sp, s);                                                \
+      case 2: return tile_##SUFFIX##_p2(shape, sp, s);                                                \
+      case 3: return tile_##SUFFIX##_p3(shape, sp, s);                                                \
+      case 4: return tile_##SUFFIX##_p4(shape, sp, s);                                                \
+    }                                                                                                 \
+    return cudaErrorInvalidValue;                                                                     \
+  }
+DGSWE_TILE_DISPATCH(fp32p64)
+DGSWE_TILE_DISPATCH(fp32p32)
+DGSWE_TILE_DISPATCH(fp32pdf)
+DGSWE_TILE_DISPATCH(fp32pir)
+cudaError_t tile_fp32pdf_p4(int, const StageParams<float>&, cudaStream_t) { return cudaErrorInvalidValue; }
 
 // the double-float velocity solve is built for p <= 3: its p = 4 entries
 // reject the call
@@ -83,8 +101,8 @@ DGSWE_AUX_DISPATCH(fp32p32)
 DGSWE_AUX_DISPATCH(fp32pdf)
 DGSWE_AUX_DISPATCH(fp32pir)
 
-// static FP64 bathymetry matrix of the mixed solve
-cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, double* ahb, cudaStream_t s) {
+// static bathymetry matrix of the mixed solve (FP64 sums stored as float pairs)
+cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, float2* ahb, cudaStream_t s) {
   const unsigned g = (unsigned)((m.E + 127) / 128);
   switch (p) {
     case 0: ahb_kernel<0><<<g, 128, 0, s>>>(m.E, hb64, ahb); break;

@@ -564,15 +564,25 @@ __device__ __forceinline__ void ldlt_solve(const PR (&L)[RefTables<P>::K][RefTab
 // Marker type of the mixed-precision solve (FP32 state only): LDL^T and both
 // triangular solves in FP32, then one step of iterative refinement,
 // x = x0 + A^{-1} r with the FP32 factors (Wilkinson's mixed-precision
-// refinement), where the residual r = b - A x0 splits A = A_hb + A_xi:
-//   A_hb = sum_n T[n][a][b] h_b,n  is static, formed once in FP64 (ahb), and
-//          its product with x0 is accumulated in FP64;
-//   A_xi = sum_n T[n][a][b] xi_n   is formed and applied in FP32, whose
-//          rounding error, eps32 |A_xi| |x0| <= eps32 (|xi| / H) |b|, stays
-//          below the FP32 rounding of the result.
-// With kappa(A) K 2^-24 << 1 the result is the FP64 solution to within FP32
-// rounding; elements whose FP32 pivots fail or spread by more than 2^10
-// (kappa estimate) take the FP64 solve.
+// refinement).  The residual r = b - A x0 must be accurate to about
+// eps32^2 |A| |x0| (it cancels to ~kappa eps32 |b|); A = A_hb + A_xi splits
+//   A_hb = sum_n T[n][a][b] h_b,n  static, formed once in FP64 and stored as
+//          an unevaluated pair of floats hi + lo (hi = fl(A_hb),
+//          lo = fl(A_hb - hi), ~48 significant bits; ahb_kernel),
+//   A_xi = sum_n T[n][a][b] xi_n   formed in FP32, whose rounding error,
+//          eps32 |A_xi| |x0| <= eps32 (|xi| / H) |b|, stays below the FP32
+//          rounding of the result.
+// Each row of the residual is a compensated dot product on the FP32 units
+// (the Dot2 scheme of Ogita, Rump and Oishi, SIAM J. Sci. Comput. 26, 2005):
+// the product hi x0_b is split exactly into its rounded value and its error
+// with a fused multiply-add, the rounded values are summed with Knuth's
+// two-sum, and every error term -- the product and sum errors and the small
+// products (lo + A_xi) x0_b -- goes to a second float, added once at the
+// end.  With kappa(A) K 2^-24 << 1 the refined result is the FP64 solution
+// to within FP32 rounding (an FP64 residual gives the same accuracy at ~8x
+// the pipe time on GB300, whose FP64 rate is 1/64 of its FP32 rate);
+// elements whose FP32 pivots fail or spread by more than 2^10 (kappa
+// estimate) take the FP64 solve.
 struct MixedIR {};
 
 template <int P, class PR, class R>
@@ -581,9 +591,27 @@ __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R
 // number of entries of the lower triangle of a K x K matrix
 __host__ __device__ constexpr int tri_size(int K) { return K * (K + 1) / 2; }
 
+// compensated running sum s + c of the refinement residual
+struct ResidualAcc {
+  float s, c;
+  __device__ __forceinline__ ResidualAcc() : s(0.f), c(0.f) {}
+  __device__ __forceinline__ explicit ResidualAcc(float b) : s(b), c(0.f) {}
+  // s + c -= (hi + t) x, with hi x split exactly (t = lo + A_xi is small)
+  __device__ __forceinline__ void sub(float hi, float t, float x) {
+    const float p = __fmul_rn(hi, x);
+    const float e = __fmaf_rn(hi, x, -p);
+    const float sn = __fsub_rn(s, p);
+    const float z = __fsub_rn(sn, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(sn, z)), __fsub_rn(-p, z));
+    s = sn;
+    c = __fmaf_rn(-t, x, __fadd_rn(c, __fsub_rn(err, e)));
+  }
+  __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
+};
+
 template <int P, class R>
 __device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, const R* U, const R* V, R* u, R* v,
-                                                    const double* __restrict__ ahb, long long E) {
+                                                    const float2* __restrict__ ahb, long long E) {
   using Tb = RefTables<P>;
   constexpr int K = Tb::K;
   float L[K][K], Dg[K], rD[K];
@@ -599,50 +627,34 @@ __device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, con
   float u0[K], v0[K];
   ldlt_solve<P>(L, rD, U, u0);
   ldlt_solve<P>(L, rD, V, v0);
-  double ru[K], rv[K], ud[K], vd[K];
-  float su[K], sv[K];   // A_xi x0 in FP32
+  ResidualAcc ru[K], rv[K];
   sfor<0, K>([&](auto n) {
-    ru[CV(n)] = double(U[CV(n)]);
-    rv[CV(n)] = double(V[CV(n)]);
-    ud[CV(n)] = double(u0[CV(n)]);
-    vd[CV(n)] = double(v0[CV(n)]);
-    su[CV(n)] = 0.f;
-    sv[CV(n)] = 0.f;
+    ru[CV(n)] = ResidualAcc(float(U[CV(n)]));
+    rv[CV(n)] = ResidualAcc(float(V[CV(n)]));
   });
   sfor<0, K>([&](auto aa) {
     constexpr int a = CV(aa);
     sfor<0, a + 1>([&](auto bb) {
       constexpr int b = CV(bb);
-      const double Ah = ahb[(long long)(a * (a + 1) / 2 + b) * E];
-      ru[a] = fma(-Ah, ud[b], ru[a]);
-      rv[a] = fma(-Ah, vd[b], rv[a]);
-      if constexpr (a != b) {
-        ru[b] = fma(-Ah, ud[a], ru[b]);
-        rv[b] = fma(-Ah, vd[a], rv[b]);
-      }
+      const float2 Ah = ahb[(long long)(a * (a + 1) / 2 + b) * E];
       float Ax = 0.f;
-      bool any = false;
       sfor<0, K>([&](auto n) {
         constexpr double t = Tb::T[CV(n)][a][b];
-        if constexpr (t != 0.0) {
-          Ax = fmaf(float(t), float(xi[CV(n)]), Ax);
-          any = true;
-        }
+        if constexpr (t != 0.0) Ax = __fmaf_rn(float(t), float(xi[CV(n)]), Ax);
       });
-      if (any) {
-        su[a] = fmaf(Ax, u0[b], su[a]);
-        sv[a] = fmaf(Ax, v0[b], sv[a]);
-        if constexpr (a != b) {
-          su[b] = fmaf(Ax, u0[a], su[b]);
-          sv[b] = fmaf(Ax, v0[a], sv[b]);
-        }
+      const float t = __fadd_rn(Ah.y, Ax);
+      ru[a].sub(Ah.x, t, u0[b]);
+      rv[a].sub(Ah.x, t, v0[b]);
+      if constexpr (a != b) {
+        ru[b].sub(Ah.x, t, u0[a]);
+        rv[b].sub(Ah.x, t, v0[a]);
       }
     });
   });
   float rf[K], du[K], dv[K];
-  sfor<0, K>([&](auto i) { rf[CV(i)] = float(ru[CV(i)] - double(su[CV(i)])); });
+  sfor<0, K>([&](auto i) { rf[CV(i)] = ru[CV(i)].get(); });
   ldlt_solve<P>(L, rD, rf, du);
-  sfor<0, K>([&](auto i) { rf[CV(i)] = float(rv[CV(i)] - double(sv[CV(i)])); });
+  sfor<0, K>([&](auto i) { rf[CV(i)] = rv[CV(i)].get(); });
   ldlt_solve<P>(L, rD, rf, dv);
   // explicit rounding: the last solve step leaves u0 = y rD, and a
   // contracted y rD + du would depend on the compilation context
@@ -653,10 +665,11 @@ __device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, con
   return true;
 }
 
-// A_hb of the mixed solve: FP64 sum_n T[n][a][b] h_b,n, n over the KB
-// bathymetry coefficients (P^max(p,1)), for b <= a
+// A_hb of the mixed solve: sum_n T[n][a][b] h_b,n in FP64, n over the KB
+// bathymetry coefficients (P^max(p,1)), for b <= a, stored as the float pair
+// (hi, lo) = (fl(A), fl(A - hi))
 template <int P>
-__global__ void ahb_kernel(long long E, const double* __restrict__ hb64, double* __restrict__ ahb) {
+__global__ void ahb_kernel(long long E, const double* __restrict__ hb64, float2* __restrict__ ahb) {
   using D = Dims<P>;
   using Tb = RefTables<D::PB>;
   constexpr int K = D::K, KB = D::KB;
@@ -673,7 +686,8 @@ __global__ void ahb_kernel(long long E, const double* __restrict__ hb64, double*
         constexpr double t = Tb::T[CV(n)][a][b];
         if constexpr (t != 0.0) A = fma(t, h[CV(n)], A);
       });
-      ahb[(long long)(a * (a + 1) / 2 + b) * E + e] = A;
+      const float hi = __double2float_rn(A);
+      ahb[(long long)(a * (a + 1) / 2 + b) * E + e] = make_float2(hi, __double2float_rn(A - double(hi)));
     });
   });
 }
@@ -757,8 +771,9 @@ struct StageParams {
   const Real* ghb;    // [2][K1][E] det-scaled bathymetry gradient coefficients
   const Real* lin;    // FP64 only: [2][K][K][E] matrices of the terms linear in xi
                       // (g xi grad h_b source + g Pi(xi h_b) pressure part)
-  const double* ahb;  // mixed solve only: [K(K+1)/2][E] FP64 matrix A of the bathymetry,
-                      // sum_n T[n][a][b] h_b,n for b <= a (row-major lower triangle)
+  const float2* ahb;  // mixed solve only: [K(K+1)/2][E] matrix A of the bathymetry,
+                      // sum_n T[n][a][b] h_b,n for b <= a (row-major lower triangle),
+                      // as float pairs hi + lo
   // time step
   double dt_fixed;    // > 0: fixed step
   double cfl_num;     // cfl * d_min / (2p + 1)
@@ -798,7 +813,7 @@ template <int NN, int P, class Real>
 __device__ __forceinline__ void dirichlet_flux(const StageParams<Real>& sp, long long e, Real nx, Real ny, Real len,
                                                const Real* tx, const Real* tU, const Real* tV, const Real* tu,
                                                const Real* tv, const Real* th, const Real* un, const Real* Hs,
-                                               Real* rb, double t_eval, unsigned& err) {
+                                               Real* rb, long long rs, double t_eval, unsigned& err) {
   constexpr int P1 = P + 1, PB1 = Dims<P>::PB1;   // h_b traces: PB1 modes
   const long long E = sp.m.E;
   const double g = double(sp.g), nxd = double(nx), nyd = double(ny);
@@ -863,7 +878,7 @@ __device__ __forceinline__ void dirichlet_flux(const StageParams<Real>& sp, long
     }
   }
   for (int f = 0; f < 3; ++f)
-    for (int j = 0; j < P1; ++j) rb[(f * P1 + j) * E] = Real(double(len) * acc[f][j]);
+    for (int j = 0; j < P1; ++j) rb[(f * P1 + j) * rs] = Real(double(len) * acc[f][j]);
 }
 
 // Side record of local edge NN of element e for the state (xi, U, V, u, v):
@@ -874,12 +889,14 @@ __device__ __forceinline__ void dirichlet_flux(const StageParams<Real>& sp, long
 //   [6P1]        max over s = 0, 1/2, 1 of |u.n| + sqrt(g H)
 // all edge polynomials in the orthonormal Legendre basis of the edge in the
 // element's own (counter-clockwise) direction.
+// The record goes to rb[k * rs], k < NREC (rs = E in HBM, the slot count in
+// shared memory).
 template <int NN, int P, int FEAT, class Real>
 __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long long e, int t, const Real* xi,
                                             const Real* U, const Real* V, const Real* u, const Real* v,
-                                            unsigned& err, double t_eval) {
+                                            unsigned& err, double t_eval, Real* rb, long long rs) {
   using D = Dims<P>;
-  constexpr int P1 = D::P1, NREC = D::NREC, PB1 = D::PB1;
+  constexpr int P1 = D::P1, PB1 = D::PB1;
   const long long E = sp.m.E;
   Real nx, ny, len;
   edge_geom<FEAT>(sp.m, e, t, NN, nx, ny, len);
@@ -904,7 +921,6 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
   });
   Real Pp[P1], PU[P1], PV[P1], un[P1];
   lprod<P>(tx, xe, Pp);
-  Real* rb = sp.rec_out + (long long)NN * NREC * E + e;
   const bool dir_edge = FEAT && sp.dirichlet && NN != 0 && neighbour(sp.m, e, NN) < 0;
   if (NN == 0 || (FEAT && (sp.m.geo || dir_edge))) {
     // general edge (the diagonal, any edge of a general mesh, a Dirichlet edge)
@@ -917,15 +933,15 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
       qn[jj] = fma(nx, tU[jj], ny * tV[jj]);
     });
     if constexpr (FEAT) {
-      if (dir_edge) dirichlet_flux<NN, P>(sp, e, nx, ny, len, tx, tU, tV, tu, tv, th, un, Hs, rb, t_eval, err);
+      if (dir_edge) dirichlet_flux<NN, P>(sp, e, nx, ny, len, tx, tU, tV, tu, tv, th, un, Hs, rb, rs, t_eval, err);
     }
     if (!dir_edge) {
       lprod2<P>(tU, tV, un, PU, PV);
       sfor<0, P1>([&](auto j) {
         constexpr int jj = CV(j);
-        rb[(0 * P1 + jj) * E] = hl * qn[jj];
-        rb[(1 * P1 + jj) * E] = hl * fma(hg * nx, Pp[jj], PU[jj]);
-        rb[(2 * P1 + jj) * E] = hl * fma(hg * ny, Pp[jj], PV[jj]);
+        rb[(0 * P1 + jj) * rs] = hl * qn[jj];
+        rb[(1 * P1 + jj) * rs] = hl * fma(hg * nx, Pp[jj], PU[jj]);
+        rb[(2 * P1 + jj) * rs] = hl * fma(hg * ny, Pp[jj], PV[jj]);
       });
     }
   } else if constexpr (NN != 0) {
@@ -937,21 +953,21 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
     sfor<0, P1>([&](auto j) {
       constexpr int jj = CV(j);
       if constexpr (NN == 1) {
-        rb[(0 * P1 + jj) * E] = sh * tU[jj];
-        rb[(1 * P1 + jj) * E] = sh * fma(hg, Pp[jj], PU[jj]);
-        rb[(2 * P1 + jj) * E] = sh * PV[jj];
+        rb[(0 * P1 + jj) * rs] = sh * tU[jj];
+        rb[(1 * P1 + jj) * rs] = sh * fma(hg, Pp[jj], PU[jj]);
+        rb[(2 * P1 + jj) * rs] = sh * PV[jj];
       } else {
-        rb[(0 * P1 + jj) * E] = sh * tV[jj];
-        rb[(1 * P1 + jj) * E] = sh * PU[jj];
-        rb[(2 * P1 + jj) * E] = sh * fma(hg, Pp[jj], PV[jj]);
+        rb[(0 * P1 + jj) * rs] = sh * tV[jj];
+        rb[(1 * P1 + jj) * rs] = sh * PU[jj];
+        rb[(2 * P1 + jj) * rs] = sh * fma(hg, Pp[jj], PV[jj]);
       }
     });
   }
   sfor<0, P1>([&](auto j) {
     constexpr int jj = CV(j);
-    rb[(3 * P1 + jj) * E] = tx[jj];
-    rb[(4 * P1 + jj) * E] = tU[jj];
-    rb[(5 * P1 + jj) * E] = tV[jj];
+    rb[(3 * P1 + jj) * rs] = tx[jj];
+    rb[(4 * P1 + jj) * rs] = tU[jj];
+    rb[(5 * P1 + jj) * rs] = tV[jj];
   });
   // wave speed of this side at s = 0, 1/2, 1 (|u.n| is sign-free)
   const Real h0 = edge_point<D::PB, 0>(Hs), h1 = edge_point<D::PB, 1>(Hs), h2 = edge_point<D::PB, 2>(Hs);
@@ -960,19 +976,27 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
   const Real l0 = fabs(u0) + sqrt(sp.g * h0);
   const Real l1 = fabs(u1) + sqrt(sp.g * h1);
   const Real l2 = fabs(u2) + sqrt(sp.g * h2);
-  rb[(6 * P1) * E] = fmax(fmax(l0, l1), l2);
+  rb[(6 * P1) * rs] = fmax(fmax(l0, l1), l2);
 }
 
 // Evaluation of one element's state: velocity projection, volume + source
 // integrals -> vs_out, side records -> rec_out; returns the element wave
 // speed |q_bar/H_bar| + sqrt(g H_bar) from the means (mean = sqrt(2) c_1).
-template <int P, class Real, class PR, int FEAT>
-__device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long long e, int t, const Real* xi,
-                                           const Real* U, const Real* V, unsigned& err, double t_eval) {
-  using D = Dims<P>;
-  constexpr int K = D::K, K1 = D::K1;
+// Element wave speed |q_bar / H_bar| + sqrt(g H_bar) from the first
+// coefficients H_0 = xi_0 + h_b,0 (in the state's precision), U_0, V_0 of an
+// element (mean = sqrt(2) c_1; the sqrt(2) cancels in the velocity).
+__device__ __forceinline__ double element_wave_speed_H(double H0, double U0, double V0, double g) {
+  const double um = U0 / H0, vm = V0 / H0;
+  return sqrt(fma(um, um, vm * vm)) + sqrt(g * 1.4142135623730951 * H0);
+}
+
+// Depth H = xi + h_b and the velocity projection of Eq. (12) of element e.
+template <int P, class Real, class PR>
+__device__ __forceinline__ void element_velocity(const StageParams<Real>& sp, long long e, const Real* xi,
+                                                 const Real* U, const Real* V, Real* hb, Real* H, Real* u, Real* v,
+                                                 unsigned& err) {
+  constexpr int K = Dims<P>::K;
   const long long E = sp.m.E;
-  Real hb[K], H[K], u[K], v[K];
   sfor<0, K>([&](auto i) {
     hb[CV(i)] = sp.hb[CV(i) * E + e];
     H[CV(i)] = xi[CV(i)] + hb[CV(i)];
@@ -983,7 +1007,17 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
   else
     solved = project_velocity<P, PR>(H, U, V, u, v);
   if (!solved) err |= ERRF_DRY;
+}
 
+// Volume + source integrals of element e (the velocity u, v already
+// projected) to vsb[(f K + a) * vss].
+template <int P, class Real, int FEAT>
+__device__ __forceinline__ void volume_to(const StageParams<Real>& sp, long long e, int t, const Real* xi,
+                                          const Real* U, const Real* V, const Real* u, const Real* v, const Real* hb,
+                                          double t_eval, Real* vsb, long long vss) {
+  using D = Dims<P>;
+  constexpr int K = D::K, K1 = D::K1;
+  const long long E = sp.m.E;
   // volume integrals (A~, grad phi_a) (Eqs. (15)-(16)): grad phi_a lies in
   // P^{p-1}, so only the first K1 coefficients of each projected product count
   constexpr bool kLin = std::is_same<Real, double>::value;
@@ -1073,35 +1107,52 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
       v1 = fma(tq, U[aa], fma(fq, V[aa], v1));
       v2 = fma(tq, V[aa], fma(-fq, U[aa], v2));
     }
-    sp.vs_out[(0 * K + aa) * E + e] = v0;
-    sp.vs_out[(1 * K + aa) * E + e] = v1;
-    sp.vs_out[(2 * K + aa) * E + e] = v2;
+    vsb[(0 * K + aa) * vss] = v0;
+    vsb[(1 * K + aa) * vss] = v1;
+    vsb[(2 * K + aa) * vss] = v2;
   });
-  side_record<0, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval);
-  side_record<1, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval);
-  side_record<2, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval);
+}
+
+// Evaluation into explicit destinations: volume + source integrals to
+// vsb[(f K + a) * vss], the side record of local edge n to
+// recb + n NREC recs with stride recs.
+template <int P, class Real, class PR, int FEAT, bool LAM = true>
+__device__ __forceinline__ double evaluate_to(const StageParams<Real>& sp, long long e, int t, const Real* xi,
+                                              const Real* U, const Real* V, unsigned& err, double t_eval, Real* vsb,
+                                              long long vss, Real* recb, long long recs) {
+  using D = Dims<P>;
+  constexpr int K = D::K, NREC = D::NREC;
+  Real hb[K], H[K], u[K], v[K];
+  element_velocity<P, Real, PR>(sp, e, xi, U, V, hb, H, u, v, err);
+  volume_to<P, Real, FEAT>(sp, e, t, xi, U, V, u, v, hb, t_eval, vsb, vss);
+  side_record<0, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval, recb + 0LL * NREC * recs, recs);
+  side_record<1, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval, recb + 1LL * NREC * recs, recs);
+  side_record<2, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval, recb + 2LL * NREC * recs, recs);
   double lam_e = 0.0;
-  if (sp.lam_next) {
-    const double Hm = double(H[0]);
-    const double um = double(U[0]) / Hm, vm = double(V[0]) / Hm;
-    lam_e = sqrt(fma(um, um, vm * vm)) + sqrt(double(sp.g) * 1.4142135623730951 * Hm);
-  }
+  if (LAM && sp.lam_next) lam_e = element_wave_speed_H(double(H[0]), double(U[0]), double(V[0]), double(sp.g));
   return lam_e;
+}
+
+// Evaluation into the launch's HBM buffers sp.vs_out and sp.rec_out.
+template <int P, class Real, class PR, int FEAT>
+__device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long long e, int t, const Real* xi,
+                                           const Real* U, const Real* V, unsigned& err, double t_eval) {
+  const long long E = sp.m.E;
+  return evaluate_to<P, Real, PR, FEAT>(sp, e, t, xi, U, V, err, t_eval, sp.vs_out + e, E, sp.rec_out + e, E);
 }
 
 // Numerical flux on local edge NN and its lift: res[f][a] -= sum_j R[NN][j][a] F^_f,j
 // with F^ = |E| (1/2 (A~(c-) + A~(c+)).n + 1/2 lambda (c- - c+)) (Lax-Friedrichs).
+// ro, rn: the element's and the neighbour's side records of the edge (entry
+// k at [k * rs]); rn = nullptr on a boundary edge.
 template <int NN, int P, int FEAT, class Real>
-__device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long long e, int t,
-                                               Real (&res)[3][Dims<P>::K]) {
+__device__ __forceinline__ void edge_flux_lift_at(const StageParams<Real>& sp, long long e, int t, const Real* ro,
+                                                  const Real* rn, long long rs, Real (&res)[3][Dims<P>::K]) {
   using D = Dims<P>;
-  constexpr int P1 = D::P1, NREC = D::NREC;
-  const long long E = sp.m.E;
-  const Real* ro = sp.rec + (long long)NN * NREC * E + e;
-  const long long f = neighbour(sp.m, e, NN);
+  constexpr int P1 = D::P1;
+  const long long E = rs;
   Real F[3][P1];
-  if (f >= 0) {
-    const Real* rn = sp.rec + (long long)NN * NREC * E + f;
+  if (rn) {
     Real nx, ny, len;
     edge_geom<FEAT>(sp.m, e, t, NN, nx, ny, len);
     const Real lam = fmax(ro[(6 * P1) * E], rn[(6 * P1) * E]);
@@ -1142,6 +1193,17 @@ __device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long
   lift_sub<NN, P>(F[0], res[0]);
   lift_sub<NN, P>(F[1], res[1]);
   lift_sub<NN, P>(F[2], res[2]);
+}
+
+template <int NN, int P, int FEAT, class Real>
+__device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long long e, int t,
+                                               Real (&res)[3][Dims<P>::K]) {
+  constexpr int NREC = Dims<P>::NREC;
+  const long long E = sp.m.E;
+  const long long f = neighbour(sp.m, e, NN);
+  const Real* ro = sp.rec + (long long)NN * NREC * E + e;
+  const Real* rn = f >= 0 ? sp.rec + (long long)NN * NREC * E + f : nullptr;
+  edge_flux_lift_at<NN, P, FEAT>(sp, e, t, ro, rn, E, res);
 }
 
 template <class Real>

@@ -135,8 +135,8 @@ cudaError_t static_fp32pdf(int p, const Mesh& m, double g, const double* hb64, v
 cudaError_t static_fp32pir(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
                            void* lin, cudaStream_t s);
 
-// static FP64 bathymetry matrix of the mixed solve: ahb [K(K+1)/2][E]
-cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, double* ahb, cudaStream_t s);
+// static bathymetry matrix of the mixed solve: ahb [K(K+1)/2][E] float pairs
+cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, float2* ahb, cudaStream_t s);
 
 // FP64 element-major [F][E][K] <-> context-precision SoA [F][K][E] on the device
 template <class Real>

