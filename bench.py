@@ -49,6 +49,7 @@ WORKLOADS = {
     "hump-p1-32": lambda: I.hump_p1_32(),
     "hump-p3-32": lambda: I.hump_p3_32(),
     "waves-p4-2048": lambda: I.waves_p4_2048(),
+    "waves-p1-512-fp32": lambda: I.waves_p2_512(p=1, precision="fp32"),
     "waves-p2-512-fp32": lambda: I.waves_p2_512(precision="fp32"),
     "waves-p3-512-fp32": lambda: I.waves_p2_512(p=3, precision="fp32"),
     "ensemble-256": lambda: I.ensemble(),
@@ -284,11 +285,13 @@ def run_batch(args, wls):
     torch.cuda.empty_cache()
     S = wls[0].rk_order
     dofs = B.dg_batch_dofs(b)
-    tiled = wls[0].precision == "fp32" and args.tile >= 0
-    shape_names = {0: "8x8 quads", 1: "16x8 quads", 2: "8x4 quads"}
-    cand_names = [shape_names[k] for k in range(3)] if tiled else ["%d elements" % k for k in (32, 64, 96, 128)]
+    tiled = wls[0].precision == "fp32" and (args.tile > 0 or (args.tile == 0 and args.proj in ("mixed", "fp32")))
+    shape_names = {1: "8x8 quads", 2: "16x8 quads", 3: "8x4 quads"}
+    cand_names = [shape_names[k] for k in (1, 2, 3)] if tiled else ["%d elements" % k for k in (32, 64, 96, 128)]
     try:
         block, tune_ms = B.dg_batch_autotune(b, 2)
+        cls_shapes = {"p%d" % q: shape_names[B.dg_batch_tile_shape(b, q)]
+                      for q in (1, 2, 3) if B.dg_batch_tile_shape(b, q)}
         B.dg_batch_run(b, args.warmup)
         if world > 1:
             torch.distributed.barrier()
@@ -338,11 +341,12 @@ def run_batch(args, wls):
                       "p_counts": {str(q): sum(1 for wl in wls if wl.p == q) for q in (1, 2, 3)},
                       "dof_per_stage": dofs, "rk_stages": S, "precision": wls[0].precision,
                       "kernel_form": "tile-fused" if tiled else "per-element",
-                      "launch_shape": shape_names[block] if tiled else "%d elements per work item" % block,
+                      "launch_shape": cls_shapes if tiled else "%d elements per work item" % block,
                       "autotune_ms_per_step": {nm: float(m) for nm, m in zip(cand_names, tune_ms) if m > 0},
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": ("instances split over %d ranks" % world) if world > 1 else "single GPU"},
-           "gpu_launches": S * args.steps, "roofline": roof,   # one persistent launch per stage
+           # one persistent launch per stage, per order class when tile-fused
+           "gpu_launches": S * args.steps * (len({wl.p for wl in wls}) if tiled else 1), "roofline": roof,
            "e2e": {"value": dofs * S / e2e_s, "unit": UNIT, "h2d_bytes_per_step": d2h, "d2h_bytes_per_step": d2h},
            "clocks": clk.summary(), "gpu": torch.cuda.get_device_name(local), "host_cores": os.cpu_count(),
            "sim_time_range": [float(min(tvals)), float(max(tvals))]}
@@ -415,8 +419,10 @@ def run_ours(args, workload=None, proj=None):
            "vs_baseline": None, "dtype": _dtype(wl.precision, args.proj),
            "data": "synthetic (seeded SplitMix64 fields, projected on device)",
            "config": {"workload": wl.name, "elements": wl.E, "p": wl.p, "K": wl.K, "rk_stages": S,
-                      "kernel_form": ("tile-fused %s quads" % {0: "8x8", 1: "16x8", 2: "8x4"}[args.tile]
-                                      if wl.precision == "fp32" and args.tile >= 0 else "per-element"),
+                      "kernel_form": ("tile-fused %s quads" % {0: "8x8", 1: "8x8", 2: "16x8", 3: "8x4"}[args.tile]
+                                      if wl.precision == "fp32" and (args.tile > 0 or (
+                                          args.tile == 0 and wl.p <= 3 and args.proj in ("mixed", "fp32")))
+                                      else "per-element"),
                       "dof_per_stage": dof_stage, "precision": wl.precision, "bc": wl.bc,
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -531,12 +537,14 @@ def main():
                     help="velocity-solve arithmetic of the FP32 state path (default: mixed for "
                          "ensemble-256, fp64 otherwise)")
     ap.add_argument("--block", type=int, default=0, help="threads per block (0 = library default)")
-    ap.add_argument("--tile", type=int, default=0, choices=[-1, 0, 1, 2],
-                    help="FP32 kernel form: tile shape 0 (8x8), 1 (16x8), 2 (8x4) quads, or -1 per-element")
+    ap.add_argument("--tile", type=int, default=0, choices=[-1, 0, 1, 2, 3],
+                    help="FP32 kernel form: 0 library default, tile shape 1 (8x8), 2 (16x8), 3 (8x4) quads, "
+                         "or -1 per-element")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--instances", type=int, default=0, help="ensemble: use only the first N instances")
+    ap.add_argument("--p-class", type=int, default=0, help="ensemble: use only the instances of this order")
     ap.add_argument("--no-fp64-plain", action="store_true",
                     help="ensemble: skip the nested plain FP64 measurement")
     args = ap.parse_args()
@@ -554,6 +562,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.workload.startswith("ensemble"):
         wls = WORKLOADS[args.workload]()
+        if args.p_class:
+            wls = [w for w in wls if w.p == args.p_class]
         out = run_batch(args, wls[:args.instances] if args.instances > 0 else wls)
         if not args.no_fp64_plain:
             # the plain FP64 path on waves-p2-512, same launch, same box

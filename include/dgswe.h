@@ -121,11 +121,13 @@ typedef struct {
                               boundary data                                    */
   int tile_shape;          /* kernel form of the time step for DG_PREC_FP32_MIXED
                               on uniform meshes without forcing (other
-                              configurations ignore it): 0 (default), 1 or 2 =
-                              tile-fused stages over 8 x 8, 16 x 8 or 8 x 4
-                              quads, intermediates in shared memory; -1 = one
-                              thread per triangle with the intermediates in
-                              HBM.
+                              configurations ignore it): 1, 2, 3 = tile-fused
+                              stages over 8 x 8, 16 x 8 or 8 x 4 quads,
+                              intermediates in shared memory; -1 = one thread
+                              per triangle with the intermediates in HBM;
+                              0 (default) = 8 x 8 tiles at p <= 3 with the
+                              MIXED and FP32 solves, one thread per triangle
+                              otherwise (measured faster there).
                               Both give the same scheme (agreeing to FP32
                               rounding); dg_rhs always uses the latter       */
 } dg_config;
@@ -274,8 +276,10 @@ dg_status dg_rhs_noalloc(const dg_config* cfg, const void* d_hb, const void* d_s
 
 /* ---- batched instances -------------------------------------------------
  * Many independent problems of uneven size and order (ensembles of
- * bathymetries and initial states) advanced together: one persistent kernel
- * launch per RK stage covers every instance, each instance keeps its own CFL
+ * bathymetries and initial states) advanced together: per RK stage one
+ * persistent kernel launch covers every instance (per-element kernels), or
+ * one per order class present (tile-fused FP32 kernels, each compiled for
+ * its order), each instance keeps its own CFL
  * time step and time, and each step is one captured CUDA graph.  The
  * per-instance arithmetic is the single-instance scheme above (same kernels'
  * element code), so results equal those of separate dg_init contexts. */
@@ -286,8 +290,9 @@ typedef struct dg_batch dg_batch;
  * for dg_init with p = 1..3, nx, ny >= 2, uniform meshes without forcing
  * (else DG_ERR_UNSUPPORTED).  All instances share precision,
  * proj_precision, rk_order, fixed-vs-CFL time stepping and the kernel form
- * (tile_shape >= 0 or -1; else DG_ERR_ARG); the initial tile shape is
- * cfgs[0]'s.  hb[i], xi[i], qx[i], qy[i]: HOST FP64 AoS arrays [E_i][K_i]
+ * (tile_shape >= 0 or -1; else DG_ERR_ARG); the kernel form and initial
+ * tile shape are cfgs[0]'s (default: tile-fused with the MIXED and FP32
+ * solves).  hb[i], xi[i], qx[i], qy[i]: HOST FP64 AoS arrays [E_i][K_i]
  * (as for dg_init; caller-owned, copied: each instance is transposed and
  * uploaded through one reused staging buffer).  Synchronises the stream.
  * Errors: DG_ERR_ARG (checked before any CUDA call), DG_ERR_UNSUPPORTED
@@ -325,19 +330,28 @@ dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double*
  * launch shape, never the arithmetic): times trial_steps steps of each
  * candidate shape, restoring the state after each, and keeps the fastest.
  * Candidates: tile-fused batches (FP32, tile_shape >= 0) tiles of 8 x 8,
- * 16 x 8 and 8 x 4 quads (128, 256, 64 triangles per CTA, shapes 0, 1, 2);
+ * 16 x 8 and 8 x 4 quads (128, 256, 64 triangles per CTA; tile_shape 1, 2,
+ * 3);
  * per-element batches 32, 64, 96 and 128 elements per work item (one thread
- * per element).  *block_out (may be NULL) receives the chosen shape index or
- * element count and ms_out (NULL or 4 doubles) the ms per step of each
- * candidate in that order (0 where there is none).  State and times are
+ * per element).  Tile-fused batches run one launch per order class and
+ * stage, and every class keeps the shape of its own fastest launches (see
+ * dg_batch_tile_shape).  *block_out (may be NULL) receives the chosen
+ * element count, or the tile shape of the highest order class, and ms_out
+ * (NULL or 4 doubles) the ms per step of each candidate in that order (all
+ * classes on that shape; 0 where there is none).  State and times are
  * unchanged on return.  Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out);
 
-/* set the launch shape of the batch (not in the paper): a tile shape 0..2
- * for tile-fused batches, else 32, 64, 96 or 128 elements per work item;
+/* set the launch shape of the batch (not in the paper): a tile shape 1..3
+ * (numbered as dg_config.tile_shape) for tile-fused batches, else 32, 64, 96 or 128 elements per work item;
  * DG_ERR_ARG otherwise.  On any error the batch keeps its previous setting.
  * Synchronises the stream. */
 dg_status dg_batch_set_block(dg_batch* b, int block);
+
+/* tile shape (dg_config.tile_shape numbering, 1..3) of the order-p class of
+ * a tile-fused batch; 0 for a per-element batch, a NULL batch, or an order
+ * without instances (not in the paper) */
+int dg_batch_tile_shape(const dg_batch* b, int p);
 
 /* degrees of freedom updated per RK stage: sum over instances of 3 K E (the
  * coefficients of xi, q_x, q_y of Eqs. (13)-(14)); 0 for NULL */

@@ -27,7 +27,7 @@ EXPORTS = ["dg_num_basis", "dg_num_basis_bathymetry", "dg_num_elements", "dg_ini
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
            "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc",
            "dg_batch_init", "dg_batch_init_device", "dg_batch_run", "dg_batch_get_state", "dg_batch_set_state", "dg_batch_autotune",
-           "dg_batch_set_block", "dg_batch_dofs", "dg_batch_destroy"]
+           "dg_batch_set_block", "dg_batch_tile_shape", "dg_batch_dofs", "dg_batch_destroy"]
 
 
 class DGError(RuntimeError):
@@ -113,6 +113,7 @@ def load(build_if_missing=True):
     lib.dg_batch_set_state.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_double]
     lib.dg_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
     lib.dg_batch_set_block.argtypes = [vp, ctypes.c_int]
+    lib.dg_batch_tile_shape.argtypes = [vp, ctypes.c_int]
     lib.dg_batch_dofs.argtypes = [vp]
     lib.dg_batch_dofs.restype = ctypes.c_longlong
     lib.dg_batch_destroy.argtypes = [vp]
@@ -338,6 +339,10 @@ def dg_batch_autotune(b, trial_steps=2):
 
 def dg_batch_set_block(b, block):
     _check(load().dg_batch_set_block(b, int(block)), "dg_batch_set_block")
+
+
+def dg_batch_tile_shape(b, p):
+    return load().dg_batch_tile_shape(b, int(p))
 
 
 def dg_batch_dofs(b):

@@ -42,7 +42,8 @@ def _units():
             # tile-fused stage kernels (FP32 state, uniform meshes)
             for p in range(0, pmax + 1):
                 out.append(("dg_tile_inst.cu", "tile_%s_p%d.o" % (sfx, p), base + ["-DDG_P=%d" % p]))
-            out.append(("dg_batch_tile_inst.cu", "batch_tile_%s.o" % sfx, base))
+            for p in (1, 2, 3):
+                out.append(("dg_batch_tile_inst.cu", "batch_tile_%s_p%d.o" % (sfx, p), base + ["-DDG_P=%d" % p]))
         # the general-mesh feature set is not built for the double-float solve
         for feat in ((0, 1) if sfx not in ("fp32pdf", "fp32pir") else (0,)):
             name = sfx + ("_gen" if feat else "")
@@ -61,7 +62,7 @@ def _cost(job):
     unit, _, defs = job
     order = max([int(d.split("=")[1]) for d in defs if d.startswith("-DDG_P=")] or [0])
     return {"dg_stage_inst.cu": 10, "dg_batch_inst.cu": 12, "dg_aux_inst.cu": 9,
-            "dg_tile_inst.cu": 11, "dg_batch_tile_inst.cu": 14}.get(unit, 0) + order + \
+            "dg_tile_inst.cu": 11, "dg_batch_tile_inst.cu": 12}.get(unit, 0) + order + \
         2 * ("-DDG_PREAL=df64" in defs)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xptxas", "-v"] + ARCH

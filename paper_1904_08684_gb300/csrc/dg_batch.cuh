@@ -48,6 +48,8 @@ struct BatchArgs {
   double alpha, beta;
   int lc;              // wave-speed slot of the current step
   int last;            // last stage: wave speed -> slot 1-lc, t += dt
+  int item_begin;      // tile-fused batches: this launch's items are
+                       // [item_begin, n_items) (one order class)
 };
 
 template <class Real, class PR, int MODE>
@@ -131,19 +133,20 @@ __global__ void __launch_bounds__(128, (stage_min_blocks<3, Real>())) batch_kern
   }
 }
 
-// Tile-fused form of the batched stage (FP32 state): work items are
-// (instance, tile) pairs, p = 3 items first; the dynamic shared memory is
-// sized for p = 3, the largest order of a batch.  The per-tile work is
-// tile_stage_body, as in the single-instance tile kernel, so results equal
-// those of single contexts with the same tile shape.
-template <class PR, int TX, int TY>
-__global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<3, TX, TY>()))
+// Tile-fused form of the batched stage (FP32 state): one persistent launch
+// per order class and RK stage, each compiled for its order P (its own
+// register budget, shared memory and tile shape); work items are
+// (instance, tile) pairs of that class, items [item_begin, n_items) of the
+// batch's list.  The per-tile work is tile_stage_body, as in the
+// single-instance tile kernel, so results equal those of single contexts.
+template <class PR, int P, int TX, int TY>
+__global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<P, TX, TY>()))
     batch_tile_kernel(const BatchArgs a) {
   extern __shared__ float tile_smem[];
   __shared__ int s_item;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
+    if (threadIdx.x == 0) s_item = a.item_begin + (int)atomicAdd(a.counter, 1u);
     __syncthreads();
     const int it = s_item;
     if (it >= a.n_items) break;
@@ -187,11 +190,7 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<3, TX,
     const int tiles_x = (d.m.nx + TX - 1) / TX;
     double lam_e = 0.0;
     unsigned err = 0;
-    switch (d.p) {
-      case 1: tile_stage_body<1, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err); break;
-      case 2: tile_stage_body<2, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err); break;
-      default: tile_stage_body<3, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err); break;
-    }
+    tile_stage_body<P, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err);
     if (lam_target) {
       const double l = block_max(lam_e);
       if (threadIdx.x == 0) atomic_max_nonneg(lam_target, l);
@@ -201,32 +200,52 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<3, TX,
   }
 }
 
-template <class PR, int TX, int TY>
+template <class PR, int P, int TX, int TY>
 cudaError_t batch_tile_launch_shape(int grid, const BatchArgs& a, cudaStream_t s) {
-  auto kern = batch_tile_kernel<PR, TX, TY>;
-  const size_t smem = sizeof(float) * tile_smem_floats<3, TX, TY>();
+  auto kern = batch_tile_kernel<PR, P, TX, TY>;
+  const size_t smem = sizeof(float) * tile_smem_floats<P, TX, TY>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, TileShape<TX, TY>::NT, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <class PR, int TX, int TY>
+template <class PR, int P, int TX, int TY>
 cudaError_t batch_tile_occupancy_shape(int* blocks_per_sm) {
-  auto kern = batch_tile_kernel<PR, TX, TY>;
-  const size_t smem = sizeof(float) * tile_smem_floats<3, TX, TY>();
+  auto kern = batch_tile_kernel<PR, P, TX, TY>;
+  const size_t smem = sizeof(float) * tile_smem_floats<P, TX, TY>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kern, TileShape<TX, TY>::NT, smem);
+}
+
+// launch / occupancy of order P with tile shape index 0..2
+template <class PR, int P>
+cudaError_t batch_tile_launch_p(int shape, int grid, const BatchArgs& a, cudaStream_t s) {
+  if (shape == 1) return batch_tile_launch_shape<PR, P, 16, 8>(grid, a, s);
+  if (shape == 2) return batch_tile_launch_shape<PR, P, 8, 4>(grid, a, s);
+  return batch_tile_launch_shape<PR, P, 8, 8>(grid, a, s);
+}
+template <class PR, int P>
+cudaError_t batch_tile_occupancy_p(int shape, int* blocks_per_sm) {
+  if (shape == 1) return batch_tile_occupancy_shape<PR, P, 16, 8>(blocks_per_sm);
+  if (shape == 2) return batch_tile_occupancy_shape<PR, P, 8, 4>(blocks_per_sm);
+  return batch_tile_occupancy_shape<PR, P, 8, 8>(blocks_per_sm);
 }
 
 // quads per tile side of each shape (kTileShapes entries)
 __host__ __device__ constexpr int tile_tx(int shape) { return shape == 1 ? 16 : 8; }
 __host__ __device__ constexpr int tile_ty(int shape) { return shape == 2 ? 4 : 8; }
 
-#define DGSWE_BATCH_TILE_DECLARE(SUFFIX)                                                               \
-  cudaError_t batch_tile_launch_##SUFFIX(int shape, int grid, const BatchArgs& a, cudaStream_t s);      \
-  cudaError_t batch_tile_occupancy_##SUFFIX(int shape, int* blocks_per_sm);
+#define DGSWE_BATCH_TILE_DECLARE_P(SUFFIX, P)                                                               \
+  cudaError_t batch_tile_launch_##SUFFIX##_p##P(int shape, int grid, const BatchArgs& a, cudaStream_t s);    \
+  cudaError_t batch_tile_occupancy_##SUFFIX##_p##P(int shape, int* blocks_per_sm);
+#define DGSWE_BATCH_TILE_DECLARE(SUFFIX)                                                                 \
+  DGSWE_BATCH_TILE_DECLARE_P(SUFFIX, 1)                                                                  \
+  DGSWE_BATCH_TILE_DECLARE_P(SUFFIX, 2)                                                                  \
+  DGSWE_BATCH_TILE_DECLARE_P(SUFFIX, 3)                                                                  \
+  cudaError_t batch_tile_launch_##SUFFIX(int p, int shape, int grid, const BatchArgs& a, cudaStream_t s);  \
+  cudaError_t batch_tile_occupancy_##SUFFIX(int p, int shape, int* blocks_per_sm);
 DGSWE_BATCH_TILE_DECLARE(fp32p64)
 DGSWE_BATCH_TILE_DECLARE(fp32p32)
 DGSWE_BATCH_TILE_DECLARE(fp32pdf)

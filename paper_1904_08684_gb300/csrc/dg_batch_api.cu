@@ -74,12 +74,16 @@ struct dg_batch {
   double* lam = nullptr;        // [2][n]
   double* t = nullptr;          // [n]
   unsigned* err = nullptr;
-  unsigned* counters = nullptr; // one per launch of a step (+ evaluation)
+  unsigned* counters = nullptr; // one per launch of a step (+ evaluation): [1 + 3 S]
   BatchInst* d_inst = nullptr;
   BatchItem* d_items = nullptr;
   int n_items = 0;
-  int block = 0, grid = 0;     // per-element: elements per item; tiled: tile shape
-  bool tiled = false;           // FP32: tile-fused stage kernels
+  int block = 0, grid = 0;     // per-element: elements per item, persistent grid
+  bool tiled = false;           // FP32: tile-fused stage kernels, one launch per order class
+  int cls_shape[4] = {0, 0, 0, 0};   // tiled, per order p = 1..3: tile shape index
+  int cls_begin[4] = {0, 0, 0, 0};   //   its items [cls_begin, cls_end)
+  int cls_end[4] = {0, 0, 0, 0};
+  int cls_grid[4] = {0, 0, 0, 0};    //   its persistent grid
   int ep = 0, lc = 0;
   bool evaluated = false;
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -88,15 +92,20 @@ struct dg_batch {
 
 namespace {
 
-cudaError_t launch_batch(const dg_batch* b, int mode, const BatchArgs& a, cudaStream_t s) {
-  if (b->tiled && mode == MODE_STAGE) {
-    switch (b->arith) {
-      case ARITH_FP32_P64: return batch_tile_launch_fp32p64(b->block, b->grid, a, s);
-      case ARITH_FP32_PDF: return batch_tile_launch_fp32pdf(b->block, b->grid, a, s);
-      case ARITH_FP32_PIR: return batch_tile_launch_fp32pir(b->block, b->grid, a, s);
-      default: return batch_tile_launch_fp32p32(b->block, b->grid, a, s);
-    }
+// tile-fused launch of order class p (items [cls_begin[p], cls_end[p]))
+cudaError_t launch_tile_class(const dg_batch* b, int p, BatchArgs a, cudaStream_t s) {
+  a.item_begin = b->cls_begin[p];
+  a.n_items = b->cls_end[p];
+  const int shape = b->cls_shape[p], grid = b->cls_grid[p];
+  switch (b->arith) {
+    case ARITH_FP32_P64: return batch_tile_launch_fp32p64(p, shape, grid, a, s);
+    case ARITH_FP32_PDF: return batch_tile_launch_fp32pdf(p, shape, grid, a, s);
+    case ARITH_FP32_PIR: return batch_tile_launch_fp32pir(p, shape, grid, a, s);
+    default: return batch_tile_launch_fp32p32(p, shape, grid, a, s);
   }
+}
+
+cudaError_t launch_batch(const dg_batch* b, int mode, const BatchArgs& a, cudaStream_t s) {
   switch (b->arith) {
     case ARITH_FP64: return batch_launch_fp64(mode, b->grid, b->block, a, s);
     case ARITH_FP32_P64: return batch_launch_fp32p64(mode, b->grid, b->block, a, s);
@@ -147,12 +156,25 @@ dg_status launch_eval(dg_batch* b, cudaStream_t s) {
   return DG_OK;
 }
 
-dg_status launch_step(const dg_batch* b, int ep, int lc, cudaStream_t s) {
-  CK(cudaMemsetAsync(b->counters + 1, 0, sizeof(unsigned) * b->S, s));
+// One step: every stage is one persistent launch (per-element batches) or
+// one per order class present (tile-fused batches, p = 3 first).  With
+// cls_ms (tile-fused only; not while capturing) each class launch is timed
+// with events and its milliseconds added to cls_ms[p].
+dg_status launch_step(const dg_batch* b, int ep, int lc, cudaStream_t s, double* cls_ms = nullptr) {
+  CK(cudaMemsetAsync(b->counters + 1, 0, sizeof(unsigned) * 3 * b->S, s));
   if (b->adaptive) CK(cudaMemsetAsync(b->lam + (size_t)(1 - lc) * b->n, 0, sizeof(double) * b->n, s));
-  for (int st = 0; st < b->S; ++st) {
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  if (cls_ms) {
+    CK(cudaEventCreate(&ev[0]));
+    const cudaError_t ce = cudaEventCreate(&ev[1]);
+    if (ce != cudaSuccess) {
+      cudaEventDestroy(ev[0]);
+      return cuda_status(ce);
+    }
+  }
+  dg_status st_out = DG_OK;
+  for (int st = 0; st < b->S && st_out == DG_OK; ++st) {
     BatchArgs a = base_args(b);
-    a.counter = b->counters + 1 + st;
     a.win = st == 0 ? 0 : st;
     a.wout = st == b->S - 1 ? 0 : st + 1;
     a.pin = (ep + st) & 1;
@@ -160,9 +182,28 @@ dg_status launch_step(const dg_batch* b, int ep, int lc, cudaStream_t s) {
     a.alpha = 1.0 - a.beta;
     a.lc = lc;
     a.last = st == b->S - 1;
-    CK(launch_batch(b, MODE_STAGE, a, s));
+    if (!b->tiled) {
+      a.counter = b->counters + 1 + st;
+      const cudaError_t ce = launch_batch(b, MODE_STAGE, a, s);
+      if (ce != cudaSuccess) st_out = cuda_status(ce);
+      continue;
+    }
+    for (int p = 3; p >= 1 && st_out == DG_OK; --p) {
+      if (b->cls_end[p] <= b->cls_begin[p]) continue;
+      a.counter = b->counters + 1 + 3 * st + (p - 1);
+      cudaError_t ce = cls_ms ? cudaEventRecord(ev[0], s) : cudaSuccess;
+      if (ce == cudaSuccess) ce = launch_tile_class(b, p, a, s);
+      if (ce == cudaSuccess && cls_ms) ce = cudaEventRecord(ev[1], s);
+      if (ce == cudaSuccess && cls_ms) ce = cudaEventSynchronize(ev[1]);
+      float ms = 0.f;
+      if (ce == cudaSuccess && cls_ms) ce = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+      if (ce != cudaSuccess) st_out = cuda_status(ce);
+      if (cls_ms) cls_ms[p] += ms;
+    }
   }
-  return DG_OK;
+  if (ev[0]) cudaEventDestroy(ev[0]);
+  if (ev[1]) cudaEventDestroy(ev[1]);
+  return st_out;
 }
 
 void drop_graphs(dg_batch* b) {
@@ -205,34 +246,49 @@ dg_status get_graph(dg_batch* b, cudaGraphExec_t* out) {
 //
 // Tiled batches (block = tile shape index): one item per tile of
 // tile_tx x tile_ty quads, in the same order of orders.
-dg_status build_items(dg_batch* b, int block) {
+dg_status build_items_impl(dg_batch* b, int block, const int* shapes) {
   std::vector<BatchItem> items;
+  int begin[4] = {0, 0, 0, 0}, end[4] = {0, 0, 0, 0};
   try {
-    for (int p = 3; p >= 1; --p)
+    for (int p = 3; p >= 1; --p) {
+      begin[p] = (int)std::min(items.size(), (size_t)INT_MAX);
       for (int i = 0; i < b->n; ++i) {
         if (b->inst[i].p != p) continue;
         if (b->tiled) {
-          const int tx = tile_tx(block), ty = tile_ty(block);
+          const int tx = tile_tx(shapes[p]), ty = tile_ty(shapes[p]);
           const long long nt = (long long)((b->inst[i].cfg.nx + tx - 1) / tx) * ((b->inst[i].cfg.ny + ty - 1) / ty);
           for (long long k = 0; k < nt; ++k) items.push_back({i, (int)k});
         } else {
           for (long long s = 0; s < b->inst[i].E; s += block) items.push_back({i, (int)s});
         }
       }
+      end[p] = (int)std::min(items.size(), (size_t)INT_MAX);
+    }
   } catch (const std::exception&) {   // no C++ exception crosses the C ABI
     return DG_ERR_OOM;
   }
   if (items.size() > (size_t)INT_MAX) return DG_ERR_ARG;
-  int occ = 0;
-  cudaError_t e;
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  int grid = 0, cls_grid[4] = {0, 0, 0, 0};
   if (b->tiled) {
-    switch (b->arith) {
-      case ARITH_FP32_P64: e = batch_tile_occupancy_fp32p64(block, &occ); break;
-      case ARITH_FP32_PDF: e = batch_tile_occupancy_fp32pdf(block, &occ); break;
-      case ARITH_FP32_PIR: e = batch_tile_occupancy_fp32pir(block, &occ); break;
-      default: e = batch_tile_occupancy_fp32p32(block, &occ); break;
+    for (int p = 1; p <= 3; ++p) {
+      if (end[p] <= begin[p]) continue;
+      int occ = 0;
+      cudaError_t e;
+      switch (b->arith) {
+        case ARITH_FP32_P64: e = batch_tile_occupancy_fp32p64(p, shapes[p], &occ); break;
+        case ARITH_FP32_PDF: e = batch_tile_occupancy_fp32pdf(p, shapes[p], &occ); break;
+        case ARITH_FP32_PIR: e = batch_tile_occupancy_fp32pir(p, shapes[p], &occ); break;
+        default: e = batch_tile_occupancy_fp32p32(p, shapes[p], &occ); break;
+      }
+      CK(e);
+      cls_grid[p] = std::max(1, std::min(end[p] - begin[p], sms * std::max(1, occ)));
     }
   } else {
+    int occ = 0;
+    cudaError_t e;
     switch (b->arith) {
       case ARITH_FP64: e = batch_occupancy_fp64(block, &occ); break;
       case ARITH_FP32_P64: e = batch_occupancy_fp32p64(block, &occ); break;
@@ -240,11 +296,9 @@ dg_status build_items(dg_batch* b, int block) {
       case ARITH_FP32_PIR: e = batch_occupancy_fp32pir(block, &occ); break;
       default: e = batch_occupancy_fp32p32(block, &occ); break;
     }
+    CK(e);
+    grid = std::max(1, std::min((int)items.size(), sms * std::max(1, occ)));
   }
-  CK(e);
-  int dev = 0, sms = 0;
-  CK(cudaGetDevice(&dev));
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   BatchItem* d_new = nullptr;
   CK(cudaMalloc(&d_new, sizeof(BatchItem) * items.size()));
   const cudaError_t ce = cudaMemcpy(d_new, items.data(), sizeof(BatchItem) * items.size(), cudaMemcpyHostToDevice);
@@ -258,8 +312,21 @@ dg_status build_items(dg_batch* b, int block) {
   b->d_items = d_new;
   b->n_items = (int)items.size();
   b->block = block;
-  b->grid = std::max(1, std::min(b->n_items, sms * std::max(1, occ)));
+  b->grid = grid;
+  for (int p = 0; p < 4; ++p) {
+    b->cls_shape[p] = shapes ? shapes[p] : 0;
+    b->cls_begin[p] = begin[p];
+    b->cls_end[p] = end[p];
+    b->cls_grid[p] = cls_grid[p];
+  }
   return DG_OK;
+}
+
+// Per-element batches: `block` elements per work item.  Tile-fused
+// batches: `block` is the tile shape index of every order class.
+dg_status build_items(dg_batch* b, int block) {
+  const int shapes[4] = {block, block, block, block};
+  return build_items_impl(b, block, b->tiled ? shapes : nullptr);
 }
 
 void free_batch(dg_batch* b) {
@@ -295,7 +362,7 @@ dg_status validate_one(const dg_config* c) {
   if (!(c->Lx > 0.0) || !(c->Ly > 0.0) || !(c->g > 0.0)) return DG_ERR_ARG;
   if (c->rk_order < 1 || c->rk_order > 3 || c->bc < 0 || c->bc > 2) return DG_ERR_ARG;
   if (c->precision < 0 || c->precision > 1 || c->proj_precision < 0 || c->proj_precision > 3) return DG_ERR_ARG;
-  if (c->tile_shape < -1 || c->tile_shape > 2) return DG_ERR_ARG;
+  if (c->tile_shape < -1 || c->tile_shape > 3) return DG_ERR_ARG;
   if (c->bc == DG_BC_DIRICHLET || c->vertex_xy || c->forcing != DG_FORCING_NONE) return DG_ERR_UNSUPPORTED;
   if (!(c->dt > 0.0) && !(c->cfl > 0.0)) return DG_ERR_ARG;
   if (2.0 * c->nx * (double)c->ny > 2.0e9) return DG_ERR_ARG;
@@ -382,7 +449,10 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
   b->S = cfgs[0].rk_order;
   b->adaptive = !(cfgs[0].dt > 0.0);
   b->stream = (cudaStream_t)stream;
-  b->tiled = b->arith != ARITH_FP64 && cfgs[0].tile_shape >= 0;
+  // tile-fused by default with the mixed and FP32 solves (as single contexts)
+  b->tiled = b->arith != ARITH_FP64 &&
+             (cfgs[0].tile_shape > 0 ||
+              (cfgs[0].tile_shape == 0 && (b->arith == ARITH_FP32_PIR || b->arith == ARITH_FP32_P32)));
   size_t ost = 0, orec = 0, ohb = 0, ohbt = 0, oghb = 0, olin = 0, oahb = 0;
   b->dofs = 0;
   for (int i = 0; i < n; ++i) {
@@ -434,7 +504,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
   alloc((void**)&b->lam, sizeof(double) * 2 * n);
   alloc((void**)&b->t, sizeof(double) * n);
   alloc((void**)&b->err, sizeof(unsigned));
-  alloc((void**)&b->counters, sizeof(unsigned) * 8);
+  alloc((void**)&b->counters, sizeof(unsigned) * 16);
   alloc((void**)&b->d_inst, sizeof(BatchInst) * n);
   if (st == DG_OK) {
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
@@ -502,7 +572,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     free_batch(b);
     return st != DG_OK ? st : cuda_status(e);
   }
-  if ((st = build_items(b, b->tiled ? (cfgs[0].tile_shape > 0 ? cfgs[0].tile_shape : 0) : 128)) != DG_OK) {
+  if ((st = build_items(b, b->tiled ? (cfgs[0].tile_shape > 1 ? cfgs[0].tile_shape - 1 : 0) : 128)) != DG_OK) {
     free_batch(b);
     return st;
   }
@@ -549,9 +619,9 @@ long long dg_batch_dofs(const dg_batch* b) { return b ? b->dofs : 0; }
 
 dg_status dg_batch_set_block(dg_batch* b, int block) {
   if (!b) return DG_ERR_ARG;
-  if (b->tiled ? (block < 0 || block >= kTileShapes) : (block < 32 || block > 128 || block % 32)) return DG_ERR_ARG;
+  if (b->tiled ? (block < 1 || block > kTileShapes) : (block < 32 || block > 128 || block % 32)) return DG_ERR_ARG;
   CK(cudaStreamSynchronize(b->stream));
-  return build_items(b, block);
+  return build_items(b, b->tiled ? block - 1 : block);
 }
 
 dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out) {
@@ -644,7 +714,9 @@ dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double*
 // batch's own state, restoring the state after each, and keeps the fastest.
 // Per-element kernels: 32, 64, 96, 128 elements per work item; tile-fused
 // kernels: tiles of 8 x 8, 16 x 8 and 8 x 4 quads (128, 256 and 64 owned
-// triangles per CTA).  ms_out[4] receives the time per step of each
+// triangles per CTA; reported as tile_shape 1, 2, 3), each order class's
+// launches timed separately (eager steps) so that every class keeps its own
+// fastest shape.  ms_out[4] receives the time per step of each
 // candidate in that order (0 where there is none).
 dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double* ms_out) {
   dgswe::NvtxRange nvtx_range("dg_batch_autotune");
@@ -661,6 +733,9 @@ dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double
     for (int c = 0; c < 4; ++c) ms_out[c] = 0.0;
   double best = 1e300;
   int best_block = b->block;
+  // tile-fused batches: each order class keeps the shape of its fastest launches
+  double cls_best[4] = {1e300, 1e300, 1e300, 1e300};
+  int cls_pick[4] = {0, 0, 0, 0};
   dg_status s = DG_OK;
   cudaError_t ce = cudaMalloc(&save, b->sz_state);
   if (ce == cudaSuccess) ce = cudaMalloc((void**)&save_t, sizeof(double) * b->n);
@@ -676,18 +751,35 @@ dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double
     b->ep = ep0;
     b->lc = lc0;
     if ((s = dg_batch_run(b, 1, nullptr)) != DG_OK) break;   // warm-up, graph build
-    ce = cudaEventRecord(e0, b->stream);
-    for (int k = 0; k < trial_steps && ce == cudaSuccess && s == DG_OK; ++k) {
-      cudaGraphExec_t g;
-      if ((s = get_graph(b, &g)) != DG_OK) break;
-      ce = cudaGraphLaunch(g, b->stream);
-      b->ep = (b->ep + b->S) & 1;
-      if (b->adaptive) b->lc = 1 - b->lc;
-    }
-    if (ce == cudaSuccess && s == DG_OK) ce = cudaEventRecord(e1, b->stream);
-    if (ce == cudaSuccess && s == DG_OK) ce = cudaEventSynchronize(e1);
     float ms = 0.f;
-    if (ce == cudaSuccess && s == DG_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (b->tiled) {
+      // eager steps, every order class's launches timed on their own
+      double cls_ms[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int k = 0; k < trial_steps && s == DG_OK; ++k) {
+        s = launch_step(b, b->ep, b->lc, b->stream, cls_ms);
+        b->ep = (b->ep + b->S) & 1;
+        if (b->adaptive) b->lc = 1 - b->lc;
+      }
+      for (int p = 1; p <= 3; ++p) {
+        ms += (float)cls_ms[p];
+        if (b->cls_end[p] > b->cls_begin[p] && cls_ms[p] < cls_best[p]) {
+          cls_best[p] = cls_ms[p];
+          cls_pick[p] = block;
+        }
+      }
+    } else {
+      ce = cudaEventRecord(e0, b->stream);
+      for (int k = 0; k < trial_steps && ce == cudaSuccess && s == DG_OK; ++k) {
+        cudaGraphExec_t g;
+        if ((s = get_graph(b, &g)) != DG_OK) break;
+        ce = cudaGraphLaunch(g, b->stream);
+        b->ep = (b->ep + b->S) & 1;
+        if (b->adaptive) b->lc = 1 - b->lc;
+      }
+      if (ce == cudaSuccess && s == DG_OK) ce = cudaEventRecord(e1, b->stream);
+      if (ce == cudaSuccess && s == DG_OK) ce = cudaEventSynchronize(e1);
+      if (ce == cudaSuccess && s == DG_OK) ce = cudaEventElapsedTime(&ms, e0, e1);
+    }
     const double per = ms / trial_steps;
     if (ms_out) ms_out[c] = per;
     if (ce == cudaSuccess && s == DG_OK && per < best) {
@@ -708,9 +800,25 @@ dg_status dg_batch_autotune(dg_batch* b, int trial_steps, int* block_out, double
   if (s != DG_OK) return s;
   if (ce != cudaSuccess) return cuda_status(ce);
   if (ce2 != cudaSuccess) return cuda_status(ce2);
-  if ((s = build_items(b, best_block)) != DG_OK) return s;
-  if (block_out) *block_out = best_block;
+  if (b->tiled) {
+    if ((s = build_items_impl(b, best_block, cls_pick)) != DG_OK) return s;
+  } else if ((s = build_items(b, best_block)) != DG_OK) {
+    return s;
+  }
+  // tile shapes are reported in dg_config.tile_shape numbering (1, 2, 3):
+  // the shape of the highest order class present
+  if (block_out) {
+    *block_out = best_block;
+    if (b->tiled)
+      for (int p = 1; p <= 3; ++p)
+        if (b->cls_end[p] > b->cls_begin[p]) *block_out = b->cls_shape[p] + 1;
+  }
   return DG_OK;
+}
+
+int dg_batch_tile_shape(const dg_batch* b, int p) {
+  if (!b || !b->tiled || p < 1 || p > 3 || b->cls_end[p] <= b->cls_begin[p]) return 0;
+  return b->cls_shape[p] + 1;
 }
 
 }  // extern "C"

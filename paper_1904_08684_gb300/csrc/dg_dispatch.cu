@@ -41,6 +41,28 @@ DGSWE_DISPATCH(fp32pir)
     }                                                                                                 \
     return cudaErrorInvalidValue;                                                                     \
   }
+#define DGSWE_BATCH_TILE_DISPATCH(SUFFIX)                                                                \
+  cudaError_t batch_tile_launch_##SUFFIX(int p, int shape, int grid, const BatchArgs& a, cudaStream_t s) { \
+    switch (p) {                                                                                        \
+      case 1: return batch_tile_launch_##SUFFIX##_p1(shape, grid, a, s);                                \
+      case 2: return batch_tile_launch_##SUFFIX##_p2(shape, grid, a, s);                                \
+      case 3: return batch_tile_launch_##SUFFIX##_p3(shape, grid, a, s);                                \
+    }                                                                                                   \
+    return cudaErrorInvalidValue;                                                                       \
+  }                                                                                                     \
+  cudaError_t batch_tile_occupancy_##SUFFIX(int p, int shape, int* blocks_per_sm) {                     \
+    switch (p) {                                                                                        \
+      case 1: return batch_tile_occupancy_##SUFFIX##_p1(shape, blocks_per_sm);                          \
+      case 2: return batch_tile_occupancy_##SUFFIX##_p2(shape, blocks_per_sm);                          \
+      case 3: return batch_tile_occupancy_##SUFFIX##_p3(shape, blocks_per_sm);                          \
+    }                                                                                                   \
+    return cudaErrorInvalidValue;                                                                       \
+  }
+DGSWE_BATCH_TILE_DISPATCH(fp32p64)
+DGSWE_BATCH_TILE_DISPATCH(fp32p32)
+DGSWE_BATCH_TILE_DISPATCH(fp32pdf)
+DGSWE_BATCH_TILE_DISPATCH(fp32pir)
+
 DGSWE_TILE_DISPATCH(fp32p64)
 DGSWE_TILE_DISPATCH(fp32p32)
 DGSWE_TILE_DISPATCH(fp32pdf)

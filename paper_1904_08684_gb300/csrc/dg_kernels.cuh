@@ -985,9 +985,18 @@ __device__ __forceinline__ void side_record(const StageParams<Real>& sp, long lo
 // Element wave speed |q_bar / H_bar| + sqrt(g H_bar) from the first
 // coefficients H_0 = xi_0 + h_b,0 (in the state's precision), U_0, V_0 of an
 // element (mean = sqrt(2) c_1; the sqrt(2) cancels in the velocity).
+// FP64 state: in FP64.  FP32 state: in FP32 (IEEE division and square root);
+// the value only enters the maximum that sets the CFL step, and FP64
+// square roots and divisions of every element cost as much FP64 pipe time
+// as a third of an FP32 stage on GB300, whose FP64 rate is 1/64 of FP32.
 __device__ __forceinline__ double element_wave_speed_H(double H0, double U0, double V0, double g) {
   const double um = U0 / H0, vm = V0 / H0;
   return sqrt(fma(um, um, vm * vm)) + sqrt(g * 1.4142135623730951 * H0);
+}
+__device__ __forceinline__ float element_wave_speed_H(float H0, float U0, float V0, float g) {
+  const float um = __fdiv_rn(U0, H0), vm = __fdiv_rn(V0, H0);
+  return __fadd_rn(__fsqrt_rn(__fmaf_rn(um, um, __fmul_rn(vm, vm))),
+                   __fsqrt_rn(__fmul_rn(__fmul_rn(g, 1.41421356f), H0)));
 }
 
 // Depth H = xi + h_b and the velocity projection of Eq. (12) of element e.
@@ -1129,7 +1138,7 @@ __device__ __forceinline__ double evaluate_to(const StageParams<Real>& sp, long 
   side_record<1, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval, recb + 1LL * NREC * recs, recs);
   side_record<2, P, FEAT>(sp, e, t, xi, U, V, u, v, err, t_eval, recb + 2LL * NREC * recs, recs);
   double lam_e = 0.0;
-  if (LAM && sp.lam_next) lam_e = element_wave_speed_H(double(H[0]), double(U[0]), double(V[0]), double(sp.g));
+  if (LAM && sp.lam_next) lam_e = double(element_wave_speed_H(H[0], U[0], V[0], sp.g));
   return lam_e;
 }
 
@@ -1147,15 +1156,16 @@ __device__ __forceinline__ double evaluate(const StageParams<Real>& sp, long lon
 // k at [k * rs]); rn = nullptr on a boundary edge.
 template <int NN, int P, int FEAT, class Real>
 __device__ __forceinline__ void edge_flux_lift_at(const StageParams<Real>& sp, long long e, int t, const Real* ro,
-                                                  const Real* rn, long long rs, Real (&res)[3][Dims<P>::K]) {
+                                                  long long ros, const Real* rn, long long rns,
+                                                  Real (&res)[3][Dims<P>::K]) {
   using D = Dims<P>;
   constexpr int P1 = D::P1;
-  const long long E = rs;
+  const long long E = ros, N = rns;
   Real F[3][P1];
   if (rn) {
     Real nx, ny, len;
     edge_geom<FEAT>(sp.m, e, t, NN, nx, ny, len);
-    const Real lam = fmax(ro[(6 * P1) * E], rn[(6 * P1) * E]);
+    const Real lam = fmax(ro[(6 * P1) * E], rn[(6 * P1) * N]);
     const Real hl = Real(0.5) * len * lam;
     // the neighbour's polynomials run the other way (s -> 1 - s flips the sign
     // of odd Legendre modes) and its fluxes use the opposite normal
@@ -1164,8 +1174,8 @@ __device__ __forceinline__ void edge_flux_lift_at(const StageParams<Real>& sp, l
       sfor<0, P1>([&](auto j) {
         constexpr int jj = CV(j);
         constexpr bool odd = (jj & 1) != 0;
-        const Real pm = ro[(fv * P1 + jj) * E], pp = rn[(fv * P1 + jj) * E];
-        const Real wm = ro[((3 + fv) * P1 + jj) * E], wp = rn[((3 + fv) * P1 + jj) * E];
+        const Real pm = ro[(fv * P1 + jj) * E], pp = rn[(fv * P1 + jj) * N];
+        const Real wm = ro[((3 + fv) * P1 + jj) * E], wp = rn[((3 + fv) * P1 + jj) * N];
         const Real phi = odd ? pm + pp : pm - pp;
         const Real jmp = odd ? wm + wp : wm - wp;
         F[fv][jj] = fma(hl, jmp, phi);
@@ -1203,7 +1213,7 @@ __device__ __forceinline__ void edge_flux_lift(const StageParams<Real>& sp, long
   const long long f = neighbour(sp.m, e, NN);
   const Real* ro = sp.rec + (long long)NN * NREC * E + e;
   const Real* rn = f >= 0 ? sp.rec + (long long)NN * NREC * E + f : nullptr;
-  edge_flux_lift_at<NN, P, FEAT>(sp, e, t, ro, rn, E, res);
+  edge_flux_lift_at<NN, P, FEAT>(sp, e, t, ro, E, rn, E, res);
 }
 
 template <class Real>
@@ -1289,12 +1299,14 @@ __device__ __forceinline__ double block_max(double v) {
 // uniform-mesh path; FEAT = 1 adds general meshes, the §3.1 body force and
 // Dirichlet edges (kept out of the fast path's registers and code).
 // Minimum resident 128-thread blocks per SM requested from the register
-// allocator (measured on GB300): FP32-state kernels run fastest at 4 (<= 128
-// registers, spilling a little), FP64 at p <= 2 at 3 (their natural fit);
-// FP64 at p >= 3 needs the full register file.
+// allocator (measured on GB300): FP32-state kernels run fastest at 6 (<= 80
+// registers: 24 warps per SM hide more of the load latency than the spills
+// to L1 cost; 6 % faster on the ensemble and 3 % on 512^2 meshes than 4
+// blocks of 128 registers), FP64 at p <= 2 at 3 (their natural fit); FP64 at
+// p >= 3 needs the full register file.
 template <int P, class Real>
 constexpr int stage_min_blocks() {
-  return std::is_same<Real, float>::value ? 4 : (P <= 2 ? 3 : 1);
+  return std::is_same<Real, float>::value ? 6 : (P <= 2 ? 3 : 1);
 }
 
 template <int P, class Real, class PR, int MODE, int FEAT>

@@ -42,26 +42,39 @@ struct TileShape {
   static constexpr int NT = NO + NH;            // threads per CTA
 };
 
-// floats of dynamic shared memory: side records [3][NREC][NT] and owned
-// volume integrals [3K][NO]
+// floats of dynamic shared memory: the owned triangles' side records
+// [3][NREC][NO], the halo triangles' one record each [NREC][NH], the owned
+// volume integrals [3K][NO] and the owned RK base state [3K][NO]
 template <int P, int TX, int TY>
 __host__ __device__ constexpr int tile_smem_floats() {
-  return 3 * Dims<P>::NREC * TileShape<TX, TY>::NT + 3 * Dims<P>::K * TileShape<TX, TY>::NO;
+  return (3 * Dims<P>::NREC + 6 * Dims<P>::K) * TileShape<TX, TY>::NO + Dims<P>::NREC * TileShape<TX, TY>::NH;
+}
+
+// 4-byte asynchronous copy global -> shared (no register is held while the
+// copy is in flight); completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 // Resident CTAs per SM requested from the register allocator: as many as
-// leave ~128 registers per thread, but no more than the shared memory of an
-// SM (227 KB per CTA at most, ~228 KB per SM) can hold.
+// leave ~128 registers per thread (~80 at p <= 1, whose element work is
+// small and whose shared memory leaves room for more CTAs), but no more than
+// the shared memory of an SM (227 KB per CTA at most, ~228 KB per SM) holds.
 template <int P, int TX, int TY>
 constexpr int tile_min_blocks() {
   constexpr int threads = (TileShape<TX, TY>::NT + 31) / 32 * 32;
-  constexpr int by_regs = 65536 / (threads * 128);
+  constexpr int by_regs = 65536 / (threads * (P <= 1 ? 80 : 128));
   constexpr int by_smem = (228 * 1024) / (4 * tile_smem_floats<P, TX, TY>() + 1024);
   constexpr int b = by_regs < by_smem ? by_regs : by_smem;
   return b > 0 ? b : 1;
 }
 
-// Tile shapes of the launchers: 0 = 8 x 8 quads, 1 = 16 x 8, 2 = 8 x 4.
+// Tile shapes of the launchers: index 0 = 8 x 8 quads, 1 = 16 x 8, 2 = 8 x 4
+// (dg_config.tile_shape 1, 2, 3).
 constexpr int kTileShapes = 3;
 
 // Halo slot h of the tile at quad (i0, j0) with valid extent TXv x TYv: the
@@ -121,9 +134,11 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
                                                 float* tile_smem, double& lam_acc, unsigned& err) {
   using D = Dims<P>;
   using TS = TileShape<TX, TY>;
-  constexpr int K = D::K, NREC = D::NREC, NO = TS::NO, NT = TS::NT;
-  float* s_rec = tile_smem;                   // [3][NREC][NT]
-  float* s_vs = tile_smem + 3 * NREC * NT;    // [3K][NO]
+  constexpr int K = D::K, NREC = D::NREC, NO = TS::NO, NH = TS::NH;
+  float* s_rec = tile_smem;                   // [3][NREC][NO] owned side records
+  float* s_hrec = s_rec + 3 * NREC * NO;      // [NREC][NH] halo side records
+  float* s_vs = s_hrec + NREC * NH;           // [3K][NO] volume integrals
+  float* s_w0 = s_vs + 3 * K * NO;            // [3K][NO] RK base state
   const int tid = threadIdx.x;
   const long long E = sp.m.E;
   const int nx = sp.m.nx, ny = sp.m.ny;
@@ -133,6 +148,13 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
   const int t = tid & 1, ii = (tid >> 1) % TX, jj = (tid >> 1) / TX;
   const bool owned = tid < NO && ii < TXv && jj < TYv;
   const long long e = 2LL * ((long long)(j0 + jj) * nx + (i0 + ii)) + t;
+  // the RK base state is needed only by the update of phase 2: its first
+  // read from HBM is issued now, asynchronously, and lands in shared memory
+  // while phase 1 computes
+  const bool with_base = sp.alpha != 0.0;
+  if (owned && with_base) {
+    sfor<0, 3 * K>([&](auto k) { cp_async4(s_w0 + CV(k) * NO + tid, sp.w0 + CV(k) * E + e); });
+  }
   // ---- phase 1: evaluation of the input state into shared memory.  Owned
   // and halo threads run the same code (one copy of the velocity solve in
   // the instruction stream); a halo triangle writes only the record of the
@@ -148,13 +170,16 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
     });
     element_velocity<P, float, PR>(sp, f, w[0], w[1], w[2], hb, H, u, v, err);
     if (owned) volume_to<P, float, 0>(sp, f, tf, w[0], w[1], w[2], u, v, hb, 0.0, s_vs + tid, NO);
-    if (owned)
-      side_record<0, P, 0>(sp, f, tf, w[0], w[1], w[2], u, v, err, 0.0, s_rec + 0 * NREC * NT + tid, NT);
+    // records: owned at s_rec (stride NO), a halo triangle's at s_hrec (stride NH)
+    float* rb = owned ? s_rec + tid : s_hrec + (tid - NO);
+    const int rs = owned ? NO : NH;
+    if (owned) side_record<0, P, 0>(sp, f, tf, w[0], w[1], w[2], u, v, err, 0.0, rb, rs);
     if (owned || n == 1)
-      side_record<1, P, 0>(sp, f, tf, w[0], w[1], w[2], u, v, err, 0.0, s_rec + 1 * NREC * NT + tid, NT);
+      side_record<1, P, 0>(sp, f, tf, w[0], w[1], w[2], u, v, err, 0.0, rb + (owned ? NREC * NO : 0), rs);
     if (owned || n == 2)
-      side_record<2, P, 0>(sp, f, tf, w[0], w[1], w[2], u, v, err, 0.0, s_rec + 2 * NREC * NT + tid, NT);
+      side_record<2, P, 0>(sp, f, tf, w[0], w[1], w[2], u, v, err, 0.0, rb + (owned ? 2 * NREC * NO : 0), rs);
   }
+  cp_async_wait_all();
   __syncthreads();
   // ---- phase 2: fluxes, lift, stage update of the owned triangles
   if (owned) {
@@ -165,9 +190,9 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
     sfor<0, 3>([&](auto nn) {
       constexpr int n = CV(nn);
       const int ns = neighbour_slot<TX, TY>(sp.m, e, ii, jj, t, n, i0, j0, TXv, TYv);
-      const float* ro = s_rec + n * NREC * NT + tid;
-      const float* rn = ns >= 0 ? s_rec + n * NREC * NT + ns : nullptr;
-      edge_flux_lift_at<n, P, 0>(sp, e, t, ro, rn, NT, res);
+      const float* ro = s_rec + n * NREC * NO + tid;
+      const float* rn = ns < 0 ? nullptr : ns < NO ? s_rec + n * NREC * NO + ns : s_hrec + (ns - NO);
+      edge_flux_lift_at<n, P, 0>(sp, e, t, ro, NO, rn, ns < NO ? NO : NH, res);
     });
     const float b = float(sp.beta), c = float(dt * sp.inv_det);
     bool fin = true;
@@ -177,8 +202,8 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
         const long long idx = (CV(f) * K + CV(i)) * E + e;
         const float wv = sp.w[idx];
         float x;
-        if (sp.alpha != 0.0) {
-          const float base = sp.w0[idx];
+        if (with_base) {
+          const float base = s_w0[(CV(f) * K + CV(i)) * NO + tid];
           x = fmaf(b, fmaf(c, res[CV(f)][CV(i)], wv - base), base);
         } else {
           x = fmaf(c, res[CV(f)][CV(i)], wv);
@@ -191,7 +216,7 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
     if (!fin) err |= ERRF_NONFINITE;
     if (sp.lam_next) {
       const float H0 = x0[0] + sp.hb[e];
-      lam_acc = fmax(lam_acc, element_wave_speed_H(double(H0), double(x0[1]), double(x0[2]), double(sp.g)));
+      lam_acc = fmax(lam_acc, double(element_wave_speed_H(H0, x0[1], x0[2], sp.g)));
     }
   }
   __syncthreads();
@@ -226,8 +251,7 @@ __global__ void __launch_bounds__(256) wave_speed_kernel(Mesh m, Real g, int K, 
   double l = 0.0;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
     const Real H0 = w[e] + hb[e];
-    l = fmax(l, element_wave_speed_H(double(H0), double(w[(long long)K * E + e]), double(w[2LL * K * E + e]),
-                                     double(g)));
+    l = fmax(l, double(element_wave_speed_H(H0, w[(long long)K * E + e], w[2LL * K * E + e], g)));
   }
   l = block_max(l);
   if (threadIdx.x == 0) atomic_max_nonneg(lam, l);

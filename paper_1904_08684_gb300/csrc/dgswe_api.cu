@@ -100,7 +100,7 @@ dg_status validate(const dg_config* c) {
   if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 128 || c->block_size % 32)) return DG_ERR_ARG;
   if (c->bc == DG_BC_PERIODIC && (c->nx < 2 || c->ny < 2)) return DG_ERR_ARG;
   if (c->forcing < 0 || c->forcing > 1) return DG_ERR_ARG;
-  if (c->tile_shape < -1 || c->tile_shape > 2) return DG_ERR_ARG;
+  if (c->tile_shape < -1 || c->tile_shape > 3) return DG_ERR_ARG;
   if (c->bc == DG_BC_DIRICHLET && c->forcing != DG_FORCING_MANUFACTURED) return DG_ERR_UNSUPPORTED;
   if (c->vertex_xy && c->bc == DG_BC_PERIODIC) return DG_ERR_UNSUPPORTED;
   // the double-float and mixed solves are built for uniform meshes without
@@ -156,7 +156,7 @@ StageParams<Real> base_params(const dg_ctx* c) {
 }
 
 cudaError_t launch_tile_any(const dg_ctx* c, const StageParams<float>& sp, cudaStream_t s) {
-  const int shape = c->cfg.tile_shape > 0 ? c->cfg.tile_shape : 0;
+  const int shape = c->cfg.tile_shape > 1 ? c->cfg.tile_shape - 1 : 0;   // launcher index
   switch (c->arith) {
     case ARITH_FP32_P64: return tile_fp32p64(c->P, shape, sp, s);
     case ARITH_FP32_PDF: return tile_fp32pdf(c->P, shape, sp, s);
@@ -488,9 +488,15 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   c->E = 2LL * cfg->nx * cfg->ny;
   c->arith = arith_of(cfg->precision, cfg->proj_precision);
   c->rsz = c->arith == ARITH_FP64 ? sizeof(double) : sizeof(float);
-  // the tile kernel covers FP32 uniform meshes without forcing (periodic or walls)
+  // the tile kernel covers FP32 uniform meshes without forcing (periodic or
+  // walls); by default with the mixed and FP32 solves at p <= 3 (at p = 4
+  // its shared memory leaves too few resident warps, and with the FP64 and
+  // double-float solves the halo's extra solves cost more than the traffic
+  // it saves: the per-element kernel measured faster there)
+  const bool light_solve = cfg->proj_precision == DG_PROJ_MIXED || cfg->proj_precision == DG_PROJ_FP32;
   c->tiled = c->arith != ARITH_FP64 && !cfg->vertex_xy && cfg->forcing == DG_FORCING_NONE &&
-             cfg->bc != DG_BC_DIRICHLET && cfg->tile_shape >= 0;
+             cfg->bc != DG_BC_DIRICHLET &&
+             (cfg->tile_shape > 0 || (cfg->tile_shape == 0 && cfg->p <= 3 && light_solve));
   c->stream = (cudaStream_t)stream;
   const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
   c->mesh = make_mesh(cfg->nx, cfg->ny, cfg->x0, cfg->y0, cfg->Lx, cfg->Ly, cfg->bc == DG_BC_PERIODIC);

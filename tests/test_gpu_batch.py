@@ -44,7 +44,7 @@ def _gpu():
 
 @pytest.mark.parametrize("precision,proj", [("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp32"), ("fp32", "df64"),
                                              ("fp32", "mixed")])
-@pytest.mark.parametrize("tile", [0, -1])
+@pytest.mark.parametrize("tile", [1, -1])
 def test_batch_equals_single_contexts(precision, proj, tile):
     """the batched persistent kernel reproduces single contexts bit for bit
     (FP32: tile-fused and per-element kernel forms)"""
@@ -95,7 +95,7 @@ def test_batch_set_state_resumes_bit_exactly():
         B.dg_batch_destroy(b2)
 
 
-@pytest.mark.parametrize("tile", [0, -1])
+@pytest.mark.parametrize("tile", [1, -1])
 def test_batch_autotune_keeps_state(tile):
     """the autotuner (tile shapes of a tile-fused batch, elements per work
     item of a per-element batch) leaves state and times as they were"""
@@ -108,7 +108,7 @@ def test_batch_autotune_keeps_state(tile):
         t1 = B.dg_batch_run(b1, 5)
         blk, ms = B.dg_batch_autotune(b2, 2)
         if tile >= 0:
-            assert blk in (0, 1, 2) and (ms[:3] > 0).all() and ms[3] == 0
+            assert blk in (1, 2, 3) and (ms[:3] > 0).all() and ms[3] == 0
         else:
             assert blk in (32, 64, 96, 128) and (ms > 0).all()
         t2 = B.dg_batch_run(b2, 5)
@@ -116,11 +116,11 @@ def test_batch_autotune_keeps_state(tile):
         for i, (_, _, E, K) in enumerate(inst):
             for a, r in zip(B.dg_batch_get_state(b2, i, E, K), B.dg_batch_get_state(b1, i, E, K)):
                 assert np.array_equal(a, r)
-        for blk in ((1, 2) if tile >= 0 else (32, 96)):
+        for blk in ((2, 3) if tile >= 0 else (32, 96)):
             B.dg_batch_set_block(b1, blk)
             B.dg_batch_run(b1, 1)
         with pytest.raises(B.DGError):
-            B.dg_batch_set_block(b1, 64 if tile >= 0 else 1)   # a shape of the other kernel form
+            B.dg_batch_set_block(b1, 64 if tile >= 0 else 2)   # a shape of the other kernel form
     finally:
         B.dg_batch_destroy(b1)
         B.dg_batch_destroy(b2)

@@ -1,6 +1,7 @@
-"""The tile-fused FP32 stage kernels (tile_shape 0, 1, 2: tiles of 8 x 8,
+"""The tile-fused FP32 stage kernels (tile_shape 1, 2, 3: tiles of 8 x 8,
 16 x 8 and 8 x 4 quads evaluating each stage's input in shared memory, with
-the neighbours across the tile boundary recomputed as a halo).
+the neighbours across the tile boundary recomputed as a halo; the default
+0 takes 8 x 8 tiles at p <= 3).
 
 * Every tile shape gives the same bits: the per-element arithmetic does not
   depend on which thread or tile computes it, a halo triangle's side record
@@ -70,8 +71,8 @@ def test_tile_shapes_give_identical_bits(oracle_mod, p, proj):
         if bc == "periodic" and min(nx, ny) < 2:
             continue
         _, fields = _inputs(oracle_mod, nx, ny, p, bc)
-        ref = _run(nx, ny, p, bc, fields, 12, 0, proj)
-        for shape in (1, 2):
+        ref = _run(nx, ny, p, bc, fields, 12, 1, proj)
+        for shape in (2, 3):
             got = _run(nx, ny, p, bc, fields, 12, shape, proj)
             assert got[0] == ref[0], (nx, ny, bc, shape)
             for a, r in zip(got[1], ref[1]):
@@ -85,7 +86,7 @@ def test_tile_and_per_element_kernels_agree(oracle_mod, p, proj):
     (20 steps, relative L2 <= 2e-6 per field, same time to 1e-6)"""
     for nx, ny, bc in SIZES[:4]:
         _, fields = _inputs(oracle_mod, nx, ny, p, bc)
-        t1, a = _run(nx, ny, p, bc, fields, 20, 0, proj)
+        t1, a = _run(nx, ny, p, bc, fields, 20, 1, proj)
         t2, b = _run(nx, ny, p, bc, fields, 20, -1, proj)
         assert abs(t1 - t2) <= 1e-6 * t2
         for x, y in zip(a, b):
@@ -101,7 +102,7 @@ def test_tile_run_matches_oracle(oracle_mod, p):
         o, fields = _inputs(oracle_mod, nx, ny, p, bc)
         xr, Ur, Vr, tr, _ = o.run(*fields, 60)
         for proj in (("mixed", "fp64") if p in (0, 4) else ("mixed",)):
-            t, (xg, Ug, Vg) = _run(nx, ny, p, bc, fields, 60, 0, proj)
+            t, (xg, Ug, Vg) = _run(nx, ny, p, bc, fields, 60, 1, proj)
             assert abs(t - tr) <= 1e-6 * tr
             for g_, r_ in ((xg, xr), (Ug, Ur), (Vg, Vr)):
                 assert _relL2(g_, r_) <= 1e-5, (nx, ny, bc, proj, _relL2(g_, r_))
@@ -119,12 +120,26 @@ def test_tile_lake_at_rest():
     hb[:, 0] = 10.0 / np.sqrt(2.0)
     z = np.zeros((E, K))
     for bc in ("periodic", "reflective"):
-        t, (x1, U1, V1) = _run(nx, ny, p, bc, (hb, z, z, z), 50, 0, "mixed")
+        t, (x1, U1, V1) = _run(nx, ny, p, bc, (hb, z, z, z), 50, 1, "mixed")
         assert t > 0 and not x1.any() and not U1.any() and not V1.any()
         xi = np.zeros((E, K))
         xi[:, 0] = 0.25 / np.sqrt(2.0)
         x0 = np.float32(xi).astype(np.float64)
-        for tile in (0, -1):
+        for tile in (1, -1):
             t, (x1, U1, V1) = _run(nx, ny, p, bc, (hb, xi, z, z), 50, tile, "mixed")
             assert np.abs(x1 - x0).max() <= 1e-6, (bc, tile, np.abs(x1 - x0).max())
             assert np.abs(U1).max() <= 1e-5 and np.abs(V1).max() <= 1e-5, (bc, tile)
+
+
+def test_default_kernel_form(oracle_mod):
+    """tile_shape 0 takes 8 x 8 tiles with the mixed and FP32 solves at
+    p <= 3 and the per-element kernels otherwise: identical bits to the
+    explicit choice in each case"""
+    nx, ny, bc = SIZES[0]
+    for p, proj, explicit in ((2, "mixed", 1), (3, "fp32", 1), (2, "fp64", -1), (3, "df64", -1), (4, "mixed", -1)):
+        _, fields = _inputs(oracle_mod, nx, ny, p, bc)
+        t0, a = _run(nx, ny, p, bc, fields, 8, 0, proj)
+        t1, b = _run(nx, ny, p, bc, fields, 8, explicit, proj)
+        assert t0 == t1, (p, proj)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y), (p, proj)

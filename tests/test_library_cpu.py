@@ -199,6 +199,7 @@ def test_null_handles_are_rejected(lib):
     assert L.dg_batch_set_state(None, 0, None, None, None, 0.0) == B.DG_ERR_ARG
     assert L.dg_batch_autotune(None, 1, None, None) == B.DG_ERR_ARG
     assert L.dg_batch_dofs(None) == 0
+    assert L.dg_batch_tile_shape(None, 3) == 0
     L.dg_destroy(None)
     L.dg_batch_destroy(None)
 
@@ -209,4 +210,14 @@ def test_friction_must_be_a_finite_nonnegative_number(lib):
     h = ctypes.c_void_p()
     for kw in (dict(tau_bf=-0.1), dict(tau_bf=float("nan")), dict(f_c=float("nan"))):
         cfg = B.make_config(4, 4, 1, **kw)
+        assert B.load().dg_init(ctypes.byref(cfg), z, z, z, z, None, ctypes.byref(h)) == B.DG_ERR_ARG
+
+
+def test_tile_shape_is_validated(lib):
+    """dg_config.tile_shape outside -1..3 is refused before any CUDA call"""
+    from paper_1904_08684_gb300 import binding as B
+    z = (ctypes.c_double * 1)()
+    h = ctypes.c_void_p()
+    for bad in (-2, 4):
+        cfg = B.make_config(4, 4, 1, precision="fp32", tile_shape=bad)
         assert B.load().dg_init(ctypes.byref(cfg), z, z, z, z, None, ctypes.byref(h)) == B.DG_ERR_ARG
