@@ -316,14 +316,20 @@ dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out);
 
 /* state of instance i (coefficients of Eqs. (13)-(14)) as host FP64 AoS
  * [E_i][K_i] arrays (each may be NULL; page-locked buffers make the copies
- * faster).  Synchronises the stream.  Errors: DG_ERR_ARG, DG_ERR_OOM,
+ * faster).  Synchronises the stream (the first call allocates the staging
+ * area described at dg_batch_set_state).  Errors: DG_ERR_ARG, DG_ERR_OOM,
  * DG_ERR_CUDA. */
 dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy);
 
 /* replace the state of instance i (coefficients of Eqs. (13)-(14), host FP64
  * AoS [E_i][K_i] arrays, all three required) and its model time t; the next
- * dg_batch_run re-evaluates the batch.  Synchronises the stream.
- * Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
+ * dg_batch_run re-evaluates the batch.  Asynchronous on the batch's stream
+ * (the copies of successive calls overlap): the arrays must stay unchanged
+ * until the stream is synchronised -- dg_batch_run, dg_batch_get_state and
+ * every other synchronising call do; page-locked arrays copy fastest.  The
+ * first call allocates a device staging area for every instance's FP64
+ * state (kept until dg_batch_destroy).  Errors: DG_ERR_ARG, DG_ERR_OOM,
+ * DG_ERR_CUDA. */
 dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double* qx, const double* qy, double t);
 
 /* Autotuner of the batched launch (not in the paper; it changes only the

@@ -144,9 +144,18 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<P, TX,
     batch_tile_kernel(const BatchArgs a) {
   extern __shared__ float tile_smem[];
   __shared__ int s_item;
+  __shared__ double s_dt;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_item = a.item_begin + (int)atomicAdd(a.counter, 1u);
+    if (threadIdx.x == 0) {
+      // the item and its instance's step, formed once for the CTA
+      const int it = a.item_begin + (int)atomicAdd(a.counter, 1u);
+      s_item = it;
+      if (it < a.n_items) {
+        const BatchInst& d0 = a.inst[a.items[it].inst];
+        s_dt = d0.dt_fixed > 0.0 ? d0.dt_fixed : d0.cfl_num / d0.lam[(long long)a.lc * a.n_inst];
+      }
+    }
     __syncthreads();
     const int it = s_item;
     if (it >= a.n_items) break;
@@ -184,16 +193,16 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<P, TX,
     sp.eq = nullptr;
     sp.nqe = 0;
     sp.lam = d.lam + (long long)a.lc * a.n_inst;
-    const double dt = d.dt_fixed > 0.0 ? d.dt_fixed : d.cfl_num / sp.lam[0];
+    const double dt = s_dt;
     double* lam_target = (a.last && !(d.dt_fixed > 0.0)) ? d.lam + (long long)(1 - a.lc) * a.n_inst : nullptr;
     sp.lam_next = lam_target;
     const int tiles_x = (d.m.nx + TX - 1) / TX;
-    double lam_e = 0.0;
+    float lam_e = 0.f;
     unsigned err = 0;
-    tile_stage_body<P, PR, TX, TY>(sp, item.start, tiles_x, dt, tile_smem, lam_e, err);
+    tile_stage_body<P, PR, TX, TY>(sp, item.start, tiles_x, tile_update(sp, dt), tile_smem, lam_e, err);
     if (lam_target) {
-      const double l = block_max(lam_e);
-      if (threadIdx.x == 0) atomic_max_nonneg(lam_target, l);
+      const float l = block_max_f(lam_e);
+      if (threadIdx.x == 0) atomic_max_nonneg(lam_target, double(l));
     }
     if (err) atomicOr(a.err, err);
     if (a.last && item.start == 0 && threadIdx.x == 0) *d.t += dt;

@@ -48,6 +48,7 @@ struct HostInst {
   int p, K, K1, P1, NREC;
   long long E;
   size_t o_state, o_rec, o_hb, o_hbt, o_ghb, o_lin, o_ahb;  // byte offsets in the arenas
+  size_t o_stage;                                            // offset (doubles) of its staging slice
 };
 
 }  // namespace
@@ -69,8 +70,9 @@ struct dg_batch {
   void* ghb = nullptr;
   void* lin = nullptr;          // FP64 batches only
   void* ahb = nullptr;          // mixed-solve batches only
-  double* stage = nullptr;      // FP64 staging for get/set state
+  double* stage = nullptr;      // FP64 staging for get/set state: one slice per instance
   size_t stage_n = 0;
+  size_t stage_total = 0;       // doubles of all slices
   double* lam = nullptr;        // [2][n]
   double* t = nullptr;          // [n]
   unsigned* err = nullptr;
@@ -340,6 +342,8 @@ void free_batch(dg_batch* b) {
   delete b;
 }
 
+__global__ void set_scalar_kernel(double* dst, double v) { *dst = v; }
+
 __global__ void cvt_f(const double* __restrict__ a, float* __restrict__ b, long long n) {
   long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = float(a[i]);
@@ -471,6 +475,8 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     h.o_ghb = oghb;
     h.o_lin = olin;
     h.o_ahb = oahb;
+    h.o_stage = b->stage_total;
+    b->stage_total += (size_t)3 * h.K * h.E;
     ost += align256((size_t)3 * h.K * h.E * b->rsz);
     orec += align256((size_t)3 * h.NREC * h.E * b->rsz);
     ohb += align256((size_t)h.K * h.E * b->rsz);
@@ -653,7 +659,9 @@ dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out) {
   return DG_OK;
 }
 
-// host FP64 staging of one instance's state [3][E][K] (grown on demand)
+// device FP64 staging of every instance's state [3][E][K] (one slice per
+// instance, allocated on first use), so that host copies of different
+// instances need not wait for each other
 static dg_status ensure_batch_stage(dg_batch* b, size_t doubles) {
   if (b->stage_n >= doubles) return DG_OK;
   if (b->stage) cudaFree(b->stage);
@@ -669,20 +677,21 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
   if (!b || i < 0 || i >= b->n) return DG_ERR_ARG;
   const HostInst& h = b->inst[i];
   const long long E = h.E, KE = (long long)h.K * E;
-  dg_status s = ensure_batch_stage(b, (size_t)3 * KE);
+  dg_status s = ensure_batch_stage(b, b->stage_total);
   if (s != DG_OK) return s;
+  double* slice = b->stage + h.o_stage;
   // device transpose to element-major FP64, then one copy per field
   const char* src = (const char*)b->w[0] + h.o_state;
   const unsigned g = (unsigned)((E + 127) / 128);
   if (b->arith == ARITH_FP64)
-    soa_to_aos_kernel<double><<<g, 128, 0, b->stream>>>((const double*)src, b->stage, E, h.K, 3);
+    soa_to_aos_kernel<double><<<g, 128, 0, b->stream>>>((const double*)src, slice, E, h.K, 3);
   else
-    soa_to_aos_kernel<float><<<g, 128, 0, b->stream>>>((const float*)src, b->stage, E, h.K, 3);
+    soa_to_aos_kernel<float><<<g, 128, 0, b->stream>>>((const float*)src, slice, E, h.K, 3);
   CK(cudaGetLastError());
   double* dst[3] = {xi, qx, qy};
   for (int f = 0; f < 3; ++f)
     if (dst[f])
-      CK(cudaMemcpyAsync(dst[f], b->stage + (size_t)f * KE, sizeof(double) * KE, cudaMemcpyDeviceToHost, b->stream));
+      CK(cudaMemcpyAsync(dst[f], slice + (size_t)f * KE, sizeof(double) * KE, cudaMemcpyDeviceToHost, b->stream));
   CK(cudaStreamSynchronize(b->stream));
   return DG_OK;
 }
@@ -692,20 +701,24 @@ dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double*
   if (!b || i < 0 || i >= b->n || !xi || !qx || !qy) return DG_ERR_ARG;
   const HostInst& h = b->inst[i];
   const long long E = h.E, KE = (long long)h.K * E;
-  dg_status s = ensure_batch_stage(b, (size_t)3 * KE);
+  dg_status s = ensure_batch_stage(b, b->stage_total);
   if (s != DG_OK) return s;
+  double* slice = b->stage + h.o_stage;
+  // asynchronous: the copies of different instances go to different slices
+  // and overlap; the caller keeps its arrays unchanged until the stream is
+  // synchronised (dg_batch_run does)
   const double* src[3] = {xi, qx, qy};
   for (int f = 0; f < 3; ++f)
-    CK(cudaMemcpyAsync(b->stage + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(slice + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, b->stream));
   char* dst = (char*)b->w[0] + h.o_state;
   const unsigned g = (unsigned)((E + 127) / 128);
   if (b->arith == ARITH_FP64)
-    aos_to_soa_kernel<double><<<g, 128, 0, b->stream>>>(b->stage, (double*)dst, E, h.K, 3);
+    aos_to_soa_kernel<double><<<g, 128, 0, b->stream>>>(slice, (double*)dst, E, h.K, 3);
   else
-    aos_to_soa_kernel<float><<<g, 128, 0, b->stream>>>(b->stage, (float*)dst, E, h.K, 3);
+    aos_to_soa_kernel<float><<<g, 128, 0, b->stream>>>(slice, (float*)dst, E, h.K, 3);
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(b->t + i, &t, sizeof(double), cudaMemcpyHostToDevice, b->stream));
-  CK(cudaStreamSynchronize(b->stream));
+  set_scalar_kernel<<<1, 1, 0, b->stream>>>(b->t + i, t);   // t by value: no host memory outlives the call
+  CK(cudaGetLastError());
   b->evaluated = false;   // the next run re-evaluates every instance
   return DG_OK;
 }

@@ -1278,6 +1278,24 @@ __device__ __forceinline__ void stage_element(const StageParams<Real>& sp, long 
   }
 }
 
+// maximum of a non-negative float over the block, valid in thread 0 (all
+// threads must call); the FP32 paths keep their wave speeds in float so that
+// no FP64 instruction is spent on the maximum
+__device__ __forceinline__ float block_max_f(float v) {
+  __shared__ float redf[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) redf[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? redf[lane] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  }
+  return v;
+}
+
 // maximum of v over the block, valid in thread 0 (all threads must call)
 __device__ __forceinline__ double block_max(double v) {
   __shared__ double red[32];

@@ -124,14 +124,30 @@ __device__ __forceinline__ int neighbour_slot(const Mesh& m, long long e, int ii
   return NO + 2 * TY + (t == 0 ? ii : TX + ii);
 }
 
+// Per-launch (per-item in a batch) constants of the stage update, formed once
+// in FP64 and rounded as stage_element rounds them: c = dt / |det B| and
+// beta; with_base = (alpha != 0).
+struct TileUpdate {
+  float c, beta;
+  bool with_base;
+};
+__device__ __forceinline__ TileUpdate tile_update(const StageParams<float>& sp, double dt) {
+  TileUpdate u;
+  u.c = float(dt * sp.inv_det);
+  u.beta = float(sp.beta);
+  u.with_base = sp.alpha != 0.0;
+  return u;
+}
+
 // One tile of one RK stage: the stage's input state sp.w is evaluated here,
 // then updated into sp.wout (w' = w0 + beta ((w - w0) + dt R),
 // R = res / |det B|, as stage_element).  All threads of the CTA call it; it
 // ends with a barrier, so the next tile may reuse the shared memory.
 // lam_acc collects the new state's element wave speeds (sp.lam_next set).
 template <int P, class PR, int TX, int TY>
-__device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, int tile, int tiles_x, double dt,
-                                                float* tile_smem, double& lam_acc, unsigned& err) {
+__device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, int tile, int tiles_x,
+                                                const TileUpdate& up, float* tile_smem, float& lam_acc,
+                                                unsigned& err) {
   using D = Dims<P>;
   using TS = TileShape<TX, TY>;
   constexpr int K = D::K, NREC = D::NREC, NO = TS::NO, NH = TS::NH;
@@ -151,7 +167,7 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
   // the RK base state is needed only by the update of phase 2: its first
   // read from HBM is issued now, asynchronously, and lands in shared memory
   // while phase 1 computes
-  const bool with_base = sp.alpha != 0.0;
+  const bool with_base = up.with_base;
   if (owned && with_base) {
     sfor<0, 3 * K>([&](auto k) { cp_async4(s_w0 + CV(k) * NO + tid, sp.w0 + CV(k) * E + e); });
   }
@@ -194,7 +210,7 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
       const float* rn = ns < 0 ? nullptr : ns < NO ? s_rec + n * NREC * NO + ns : s_hrec + (ns - NO);
       edge_flux_lift_at<n, P, 0>(sp, e, t, ro, NO, rn, ns < NO ? NO : NH, res);
     });
-    const float b = float(sp.beta), c = float(dt * sp.inv_det);
+    const float b = up.beta, c = up.c;
     bool fin = true;
     float x0[3];
     sfor<0, 3>([&](auto f) {
@@ -216,7 +232,7 @@ __device__ __forceinline__ void tile_stage_body(const StageParams<float>& sp, in
     if (!fin) err |= ERRF_NONFINITE;
     if (sp.lam_next) {
       const float H0 = x0[0] + sp.hb[e];
-      lam_acc = fmax(lam_acc, double(element_wave_speed_H(H0, x0[1], x0[2], sp.g)));
+      lam_acc = fmaxf(lam_acc, element_wave_speed_H(H0, x0[1], x0[2], sp.g));
     }
   }
   __syncthreads();
@@ -228,13 +244,14 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<P, TX,
     tile_stage_kernel(const StageParams<float> sp, int tiles_x, int n_tiles) {
   extern __shared__ float tile_smem[];
   const double dt = sp.dt_fixed > 0.0 ? sp.dt_fixed : sp.cfl_num / sp.lam[0];
-  double lam_acc = 0.0;
+  const TileUpdate up = tile_update(sp, dt);
+  float lam_acc = 0.f;
   unsigned err = 0;
   for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x)
-    tile_stage_body<P, PR, TX, TY>(sp, tile, tiles_x, dt, tile_smem, lam_acc, err);
+    tile_stage_body<P, PR, TX, TY>(sp, tile, tiles_x, up, tile_smem, lam_acc, err);
   if (sp.lam_next) {
-    const double l = block_max(lam_acc);
-    if (threadIdx.x == 0) atomic_max_nonneg(sp.lam_next, l);
+    const float l = block_max_f(lam_acc);
+    if (threadIdx.x == 0) atomic_max_nonneg(sp.lam_next, double(l));
   }
   if (err) atomicOr(sp.err, err);
 }
