@@ -17,9 +17,14 @@ the oracle's.
 
 Tolerances.  FP32 rounding in the RHS enters through the volume and edge
 integrals, each O(|F| / h) per unit area, which cancel to the O(|grad F|)
-right-hand side: relative to max |R| the rounding error grows like 1/h.  The
-small-mesh FP32 test holds 2e-5 at h = 1/13; at h = 1/2048 the same
-arithmetic gives 2e-5 * 2048 / 13 = 3.2e-3 (relative L2 over the samples).
+right-hand side, so its relative size grows like 1/h.  At p = 4 on 2048^2
+the bar is measured, not assumed: the oracle's RHS is re-evaluated with
+every input coefficient perturbed by a random relative 2^-24 (one FP32
+rounding), and that sensitivity s (per field) is the floor any FP32
+evaluation sits on; the FP32 path, which rounds O(100) such terms per
+coefficient, must stay within 16 s (16 = sqrt(256), the growth of
+independent roundings), and within 4x of its own distance from the GPU's
+FP64 path on the same inputs.
 After one SSP-RK3 step from q = 0 the momentum is a pure increment dt R, so
 its relative L2 error is the RHS error again (bar as above at the instance's
 h); the depth field, whose increment is tiny against its value, is held to
@@ -90,23 +95,37 @@ def test_large_instance_p4_2048_rhs_sampled(oracle_mod, proj):
                                    U0=lambda x, y: 0.4 + 0.2 * np.sin(2 * np.pi * (x - y)),
                                    V0=lambda x, y: -0.25 + 0.1 * np.cos(4 * np.pi * x))
     ref = o.rhs(hb, xi, U, V, elems=S)[:, S, :]
-    cfg = B.make_config(wl.nx, wl.ny, wl.p, bc="periodic", precision="fp32", rk_order=3, cfl=wl.cfl,
-                        proj_precision=proj)
-    ctx = B.dg_init(cfg, hb, xi, U, V)
-    try:
-        Si = torch.from_numpy(S.astype(np.int64)).cuda()
-        st = torch.empty((3, o.K, E), dtype=torch.float32, device="cuda")
-        for f, a in enumerate((xi, U, V)):
-            st[f] = torch.from_numpy(a.T.astype(np.float32)).cuda()
-        out = torch.empty_like(st)
-        B.dg_rhs(ctx, st, out)
-        got = out[:, :, Si].double().cpu().numpy().transpose(0, 2, 1)
-    finally:
-        B.dg_destroy(ctx)
-    bar = 2e-5 * wl.nx / 13
-    errs = [_rel(got[f], ref[f]) for f in range(3)]
-    print("p4-2048 FP32 (%s solve) RHS relative L2 per field:" % proj, errs)
-    assert max(errs) <= bar, (errs, bar)
+    # sensitivity of the RHS to one FP32 rounding of every input coefficient
+    rng2 = np.random.default_rng(24)
+
+    def jitter(a):
+        return a * (1.0 + 2.0 ** -24 * rng2.uniform(-1.0, 1.0, a.shape))
+    refj = o.rhs(jitter(hb), jitter(xi), jitter(U), jitter(V), elems=S)[:, S, :]
+    sens = [_rel(refj[f], ref[f]) for f in range(3)]
+    Si = torch.from_numpy(S.astype(np.int64)).cuda()
+    got = {}
+    for prec, dtype in (("fp32", torch.float32), ("fp64", torch.float64)):
+        cfg = B.make_config(wl.nx, wl.ny, wl.p, bc="periodic", precision=prec, rk_order=3, cfl=wl.cfl,
+                            proj_precision=proj)
+        ctx = B.dg_init(cfg, hb, xi, U, V)
+        try:
+            st = torch.empty((3, o.K, E), dtype=dtype, device="cuda")
+            for f, a in enumerate((xi, U, V)):
+                st[f] = torch.from_numpy(a.T.copy()).to(dtype).cuda()
+            out = torch.empty_like(st)
+            B.dg_rhs(ctx, st, out)
+            got[prec] = out[:, :, Si].double().cpu().numpy().transpose(0, 2, 1)
+        finally:
+            B.dg_destroy(ctx)
+            del st, out
+            torch.cuda.empty_cache()
+    errs = [_rel(got["fp32"][f], ref[f]) for f in range(3)]
+    disc = [_rel(got["fp32"][f], got["fp64"][f]) for f in range(3)]
+    print("p4-2048 FP32 (%s solve) RHS relative L2 per field: %s; FP32 vs GPU FP64 %s; "
+          "input-rounding sensitivity %s" % (proj, errs, disc, sens))
+    for f in range(3):
+        assert errs[f] <= 16 * sens[f], (f, errs, sens)
+        assert errs[f] <= 4 * disc[f] + 1e-12, (f, errs, disc)
 
 
 @pytest.mark.parametrize("proj", ["fp64", "mixed"])
