@@ -74,8 +74,8 @@ typedef enum { DG_PREC_FP64 = 0, DG_PREC_FP32_MIXED = 1 } dg_precision;
  * FP64 (default); FP32; double-float (pairs of FP32 numbers, ~48 significant
  * bits, on the FP32 units; p <= 3); or MIXED: FP32 LDL^T and solves plus one
  * step of iterative refinement whose residual is accurate to ~48 bits (a
- * compensated FP32 dot product with the static bathymetry matrix kept as
- * float pairs), which returns the FP64 solution to within FP32 rounding
+ * compensated FP32 dot product; the static bathymetry matrix is its FP32
+ * part, recomputed, plus a stored FP32 low part), which returns the FP64 solution to within FP32 rounding
  * while the FP32 factors hold (elements whose FP32 pivots fail or spread by
  * more than 2^10 take the FP64 solve).  DF64 and MIXED: uniform meshes
  * without forcing only. */
@@ -259,7 +259,8 @@ enum { DG_FLAG_DRY = 1u /* a non-positive (or NaN) depth at a wave-speed point, 
  * Intermediates live in one fixed 32 MiB array inside the library's device
  * image, reserved on every GPU that loads the library until the process
  * exits.  A mesh needs about (K + 3(p+1) + p(p+1) + 3K + 3(6p+7)) words per
- * triangle, plus 2K^2 in FP64, plus K(K+1)/2 FP64 words with DG_PROJ_MIXED
+ * triangle, plus 2K^2 in FP64, plus K(K+1)/2 FP32 words (twice that at p = 4)
+ * with DG_PROJ_MIXED
  * (8 bytes FP64, 4 bytes FP32, each block rounded up to 256 bytes); meshes
  * that do not fit are rejected with DG_ERR_ARG before any GPU work (about
  * 24,000 triangles at p = 2 in FP64).  The first call on a device looks up

@@ -27,7 +27,7 @@ struct BatchInst {
   const void* hbt;
   const void* ghb;
   const void* lin;     // FP64 batches: [2][K][K][E], else null
-  const float2* ahb;   // mixed-solve batches: [K(K+1)/2][E] float pairs, else null
+  const float* ahb;    // mixed-solve batches: [ahb_words(K)][E] parts of A_hb, else null
   double* lam;         // slot s of this instance at lam[s * n_inst]
   double* t;
   int p;
@@ -53,7 +53,7 @@ struct BatchArgs {
 };
 
 template <class Real, class PR, int MODE>
-__global__ void __launch_bounds__(128, (stage_min_blocks<3, Real>())) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(128, (stage_min_blocks<3, Real, PR>())) batch_kernel(const BatchArgs a) {
   __shared__ int s_item;
   for (;;) {
     __syncthreads();
@@ -145,15 +145,21 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<P, TX,
   extern __shared__ float tile_smem[];
   __shared__ int s_item;
   __shared__ double s_dt;
+  __shared__ TileUpdate s_up;
   for (;;) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      // the item and its instance's step, formed once for the CTA
+      // the item, its instance's step and the update constants, formed once
+      // for the CTA (as tile_update forms them)
       const int it = a.item_begin + (int)atomicAdd(a.counter, 1u);
       s_item = it;
       if (it < a.n_items) {
         const BatchInst& d0 = a.inst[a.items[it].inst];
-        s_dt = d0.dt_fixed > 0.0 ? d0.dt_fixed : d0.cfl_num / d0.lam[(long long)a.lc * a.n_inst];
+        const double dt0 = d0.dt_fixed > 0.0 ? d0.dt_fixed : d0.cfl_num / d0.lam[(long long)a.lc * a.n_inst];
+        s_dt = dt0;
+        s_up.c = float(dt0 * d0.inv_det);
+        s_up.beta = float(a.beta);
+        s_up.with_base = a.alpha != 0.0;
       }
     }
     __syncthreads();
@@ -199,7 +205,8 @@ __global__ void __launch_bounds__(TileShape<TX, TY>::NT, (tile_min_blocks<P, TX,
     const int tiles_x = (d.m.nx + TX - 1) / TX;
     float lam_e = 0.f;
     unsigned err = 0;
-    tile_stage_body<P, PR, TX, TY>(sp, item.start, tiles_x, tile_update(sp, dt), tile_smem, lam_e, err);
+    const TileUpdate up = s_up;
+    tile_stage_body<P, PR, TX, TY>(sp, item.start, tiles_x, up, tile_smem, lam_e, err);
     if (lam_target) {
       const float l = block_max_f(lam_e);
       if (threadIdx.x == 0) atomic_max_nonneg(lam_target, double(l));

@@ -483,7 +483,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     ohbt += align256((size_t)3 * h.P1 * h.E * b->rsz);
     oghb += align256((size_t)2 * h.K1 * h.E * b->rsz);
     if (b->arith == ARITH_FP64) olin += align256((size_t)2 * h.K * h.K * h.E * b->rsz);
-    if (b->arith == ARITH_FP32_PIR) oahb += align256(sizeof(float2) * tri_size(h.K) * h.E);
+    if (b->arith == ARITH_FP32_PIR) oahb += align256(sizeof(float) * ahb_words(h.K) * h.E);
     b->dofs += 3LL * h.K * h.E;
     b->inst.push_back(h);
   }
@@ -547,7 +547,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
     d.hbt = (char*)b->hbt + h.o_hbt;
     d.ghb = (char*)b->ghb + h.o_ghb;
     d.lin = b->lin ? (char*)b->lin + h.o_lin : nullptr;
-    d.ahb = b->ahb ? (const float2*)((char*)b->ahb + h.o_ahb) : nullptr;
+    d.ahb = b->ahb ? (const float*)((char*)b->ahb + h.o_ahb) : nullptr;
     d.lam = b->lam + i;
     d.t = b->t + i;
     d.p = h.p;
@@ -566,7 +566,7 @@ dg_status batch_create(int n, const dg_config* cfgs, InputSource& src, void* str
       case ARITH_FP32_PDF: e = static_fp32pdf(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
       case ARITH_FP32_PIR:
         e = static_fp32pir(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s);
-        if (e == cudaSuccess) e = static_ahb(h.p, d.m, hbi, (float2*)d.ahb, s);
+        if (e == cudaSuccess) e = static_ahb(h.p, d.m, hbi, (float*)d.ahb, s);
         break;
       default: e = static_fp32p32(h.p, d.m, h.cfg.g, hbi, ph, pt, pg, nullptr, s); break;
     }

@@ -124,7 +124,7 @@ DGSWE_AUX_DISPATCH(fp32pdf)
 DGSWE_AUX_DISPATCH(fp32pir)
 
 // static bathymetry matrix of the mixed solve (FP64 sums stored as float pairs)
-cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, float2* ahb, cudaStream_t s) {
+cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, float* ahb, cudaStream_t s) {
   const unsigned g = (unsigned)((m.E + 127) / 128);
   switch (p) {
     case 0: ahb_kernel<0><<<g, 128, 0, s>>>(m.E, hb64, ahb); break;

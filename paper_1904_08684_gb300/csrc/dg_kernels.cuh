@@ -65,6 +65,10 @@ struct Mesh {
   double diag;     // sqrt(hx^2 + hy^2)
   double ndx, ndy; // hy / diag, hx / diag: unit normal of the lower diagonal
   int periodic;    // 1 periodic, 0 walls
+  // the same sizes rounded to FP32 once on the host: the FP32 kernels read
+  // them instead of converting the doubles per use (a double -> float
+  // conversion runs on GB300's FP64 pipe, 1/64 of the FP32 rate)
+  float fhx, fhy, fdiag, fndx, fndy;
   // per-element geometry of a general (e.g. randomly perturbed) quad-split
   // mesh, [NGEO][E] FP64; null for the uniform mesh (computed from e)
   const double* geo;
@@ -92,6 +96,13 @@ __device__ __forceinline__ long long neighbour(const Mesh& m, long long e, int n
   return 2 * ((long long)jj * m.nx + ii) + (1 - t);
 }
 
+// a mesh size in the kernel's precision: the double, or its float copy
+template <class Real>
+__device__ __forceinline__ Real mesh_val(double d, float f) {
+  if constexpr (std::is_same<Real, float>::value) return f;
+  else return Real(d);
+}
+
 // Outward unit normal and length of local edge n.  Lower triangle: edge 0 is
 // the diagonal (normal (hy, hx)/diag), edge 1 the left side (-1, 0), edge 2
 // the bottom (0, -1); the upper triangle has the opposite normals.
@@ -105,17 +116,17 @@ __device__ __forceinline__ void edge_geom(const Mesh& m, long long e, int t, int
   }
   const Real s = t ? Real(-1) : Real(1);
   if (n == 0) {
-    nx = s * Real(m.ndx);
-    ny = s * Real(m.ndy);
-    len = Real(m.diag);
+    nx = s * mesh_val<Real>(m.ndx, m.fndx);
+    ny = s * mesh_val<Real>(m.ndy, m.fndy);
+    len = mesh_val<Real>(m.diag, m.fdiag);
   } else if (n == 1) {
     nx = -s;
     ny = Real(0);
-    len = Real(m.hy);
+    len = mesh_val<Real>(m.hy, m.fhy);
   } else {
     nx = Real(0);
     ny = -s;
-    len = Real(m.hx);
+    len = mesh_val<Real>(m.hx, m.fhx);
   }
 }
 
@@ -132,8 +143,8 @@ __device__ __forceinline__ void elem_G(const Mesh& m, long long e, int t, Real& 
     return;
   }
   const Real sgn = t ? Real(-1) : Real(1);
-  G11 = sgn * Real(m.hy);
-  G22 = sgn * Real(m.hx);
+  G11 = sgn * mesh_val<Real>(m.hy, m.fhy);
+  G22 = sgn * mesh_val<Real>(m.hx, m.fhx);
   G12 = Real(0);
   G21 = Real(0);
 }
@@ -566,9 +577,12 @@ __device__ __forceinline__ void ldlt_solve(const PR (&L)[RefTables<P>::K][RefTab
 // x = x0 + A^{-1} r with the FP32 factors (Wilkinson's mixed-precision
 // refinement).  The residual r = b - A x0 must be accurate to about
 // eps32^2 |A| |x0| (it cancels to ~kappa eps32 |b|); A = A_hb + A_xi splits
-//   A_hb = sum_n T[n][a][b] h_b,n  static, formed once in FP64 and stored as
-//          an unevaluated pair of floats hi + lo (hi = fl(A_hb),
-//          lo = fl(A_hb - hi), ~48 significant bits; ahb_kernel),
+//   A_hb = sum_n T[n][a][b] h_b,n  static: its FP64 value is kept as the
+//          unevaluated sum hi + lo, hi the FP32 sum of the FP32 bathymetry
+//          coefficients formed by one fixed sequence of rounded operations
+//          (ahb_hi: recomputed in the solve; stored at p = 4, see
+//          ahb_keeps_hi), lo = fl(A_hb - hi) stored once per context
+//          (ahb_kernel), ~48 significant bits for 4 bytes per entry;
 //   A_xi = sum_n T[n][a][b] xi_n   formed in FP32, whose rounding error,
 //          eps32 |A_xi| |x0| <= eps32 (|xi| / H) |b|, stays below the FP32
 //          rounding of the result.
@@ -591,6 +605,13 @@ __device__ __forceinline__ bool project_velocity(const R* H, const R* U, const R
 // number of entries of the lower triangle of a K x K matrix
 __host__ __device__ constexpr int tri_size(int K) { return K * (K + 1) / 2; }
 
+// The mixed solve's A_hb = hi + lo per entry: lo is stored; hi is recomputed
+// from h_b for p <= 3 (at p = 3, 226 FMAs per triangle against 55 loads) and
+// stored too at p = 4 (K = 15), where the recompute takes 636 FMAs against
+// 120 loads and measured slower than the loads.  FP32 words per triangle:
+__host__ __device__ constexpr bool ahb_keeps_hi(int K) { return K >= 15; }
+__host__ __device__ constexpr int ahb_words(int K) { return tri_size(K) * (ahb_keeps_hi(K) ? 2 : 1); }
+
 // compensated running sum s + c of the refinement residual
 struct ResidualAcc {
   float s, c;
@@ -609,9 +630,22 @@ struct ResidualAcc {
   __device__ __forceinline__ float get() const { return __fadd_rn(s, c); }
 };
 
+// hi of entry (a, b) of A_hb from the FP32 bathymetry coefficients hb[n],
+// n < K: the same rounded operations in ahb_kernel and in the solve
+template <int P, int a, int b>
+__device__ __forceinline__ float ahb_hi(const float* hb) {
+  using Tb = RefTables<P>;
+  float hi = 0.f;
+  sfor<0, Tb::K>([&](auto n) {
+    constexpr double t = Tb::T[CV(n)][a][b];
+    if constexpr (t != 0.0) hi = __fmaf_rn(float(t), hb[CV(n)], hi);
+  });
+  return hi;
+}
+
 template <int P, class R>
-__device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, const R* U, const R* V, R* u, R* v,
-                                                    const float2* __restrict__ ahb, long long E) {
+__device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, const R* hb, const R* U, const R* V,
+                                                    R* u, R* v, const float* __restrict__ ahb, long long E) {
   using Tb = RefTables<P>;
   constexpr int K = Tb::K;
   float L[K][K], Dg[K], rD[K];
@@ -636,18 +670,22 @@ __device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, con
     constexpr int a = CV(aa);
     sfor<0, a + 1>([&](auto bb) {
       constexpr int b = CV(bb);
-      const float2 Ah = ahb[(long long)(a * (a + 1) / 2 + b) * E];
+      constexpr int ab = a * (a + 1) / 2 + b;
+      const float lo = ahb[(long long)ab * E];
+      float hi;
+      if constexpr (ahb_keeps_hi(K)) hi = ahb[(long long)(tri_size(K) + ab) * E];
+      else hi = ahb_hi<P, a, b>(hb);
       float Ax = 0.f;
       sfor<0, K>([&](auto n) {
         constexpr double t = Tb::T[CV(n)][a][b];
         if constexpr (t != 0.0) Ax = __fmaf_rn(float(t), float(xi[CV(n)]), Ax);
       });
-      const float t = __fadd_rn(Ah.y, Ax);
-      ru[a].sub(Ah.x, t, u0[b]);
-      rv[a].sub(Ah.x, t, v0[b]);
+      const float t = __fadd_rn(lo, Ax);
+      ru[a].sub(hi, t, u0[b]);
+      rv[a].sub(hi, t, v0[b]);
       if constexpr (a != b) {
-        ru[b].sub(Ah.x, t, u0[a]);
-        rv[b].sub(Ah.x, t, v0[a]);
+        ru[b].sub(hi, t, u0[a]);
+        rv[b].sub(hi, t, v0[a]);
       }
     });
   });
@@ -665,18 +703,22 @@ __device__ __forceinline__ bool project_velocity_ir(const R* H, const R* xi, con
   return true;
 }
 
-// A_hb of the mixed solve: sum_n T[n][a][b] h_b,n in FP64, n over the KB
-// bathymetry coefficients (P^max(p,1)), for b <= a, stored as the float pair
-// (hi, lo) = (fl(A), fl(A - hi))
+// A_hb of the mixed solve: A = sum_n T[n][a][b] h_b,n in FP64, n over the KB
+// bathymetry coefficients (P^max(p,1)), for b <= a; stored is
+// lo = fl(A - hi) at [ab][E] (ab = a(a+1)/2 + b) with hi = ahb_hi of the
+// FP32 coefficients (the rounding of h_b that the FP32 contexts hold), or,
+// where ahb_keeps_hi, hi = fl(A) stored at [K(K+1)/2 + ab][E]
 template <int P>
-__global__ void ahb_kernel(long long E, const double* __restrict__ hb64, float2* __restrict__ ahb) {
+__global__ void ahb_kernel(long long E, const double* __restrict__ hb64, float* __restrict__ ahb) {
   using D = Dims<P>;
   using Tb = RefTables<D::PB>;
   constexpr int K = D::K, KB = D::KB;
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   double h[KB];
+  float hf[K];
   sfor<0, KB>([&](auto i) { h[CV(i)] = hb64[CV(i) * E + e]; });
+  sfor<0, K>([&](auto i) { hf[CV(i)] = float(h[CV(i)]); });
   sfor<0, K>([&](auto aa) {
     constexpr int a = CV(aa);
     sfor<0, a + 1>([&](auto bb) {
@@ -686,8 +728,15 @@ __global__ void ahb_kernel(long long E, const double* __restrict__ hb64, float2*
         constexpr double t = Tb::T[CV(n)][a][b];
         if constexpr (t != 0.0) A = fma(t, h[CV(n)], A);
       });
-      const float hi = __double2float_rn(A);
-      ahb[(long long)(a * (a + 1) / 2 + b) * E + e] = make_float2(hi, __double2float_rn(A - double(hi)));
+      constexpr int ab = a * (a + 1) / 2 + b;
+      if constexpr (ahb_keeps_hi(K)) {
+        const float hi = __double2float_rn(A);
+        ahb[(long long)ab * E + e] = __double2float_rn(A - double(hi));
+        ahb[(long long)(tri_size(K) + ab) * E + e] = hi;
+      } else {
+        const float hi = ahb_hi<P, a, b>(hf);
+        ahb[(long long)ab * E + e] = __double2float_rn(A - double(hi));
+      }
     });
   });
 }
@@ -771,9 +820,10 @@ struct StageParams {
   const Real* ghb;    // [2][K1][E] det-scaled bathymetry gradient coefficients
   const Real* lin;    // FP64 only: [2][K][K][E] matrices of the terms linear in xi
                       // (g xi grad h_b source + g Pi(xi h_b) pressure part)
-  const float2* ahb;  // mixed solve only: [K(K+1)/2][E] matrix A of the bathymetry,
-                      // sum_n T[n][a][b] h_b,n for b <= a (row-major lower triangle),
-                      // as float pairs hi + lo
+  const float* ahb;   // mixed solve only: [ahb_words(K)][E] low parts lo (and at p = 4
+                      // the FP32 parts) of the matrix A of the bathymetry,
+                      // sum_n T[n][a][b] h_b,n for b <= a (row-major lower
+                      // triangle; see ahb_kernel)
   // time step
   double dt_fixed;    // > 0: fixed step
   double cfl_num;     // cfl * d_min / (2p + 1)
@@ -1012,7 +1062,7 @@ __device__ __forceinline__ void element_velocity(const StageParams<Real>& sp, lo
   });
   bool solved;
   if constexpr (std::is_same<PR, MixedIR>::value)
-    solved = project_velocity_ir<P>(H, xi, U, V, u, v, sp.ahb + e, E);
+    solved = project_velocity_ir<P>(H, xi, hb, U, V, u, v, sp.ahb + e, E);
   else
     solved = project_velocity<P, PR>(H, U, V, u, v);
   if (!solved) err |= ERRF_DRY;
@@ -1320,15 +1370,17 @@ __device__ __forceinline__ double block_max(double v) {
 // allocator (measured on GB300): FP32-state kernels run fastest at 6 (<= 80
 // registers: 24 warps per SM hide more of the load latency than the spills
 // to L1 cost; 6 % faster on the ensemble and 3 % on 512^2 meshes than 4
-// blocks of 128 registers), FP64 at p <= 2 at 3 (their natural fit); FP64 at
-// p >= 3 needs the full register file.
-template <int P, class Real>
+// blocks of 128 registers), except with the FP64 velocity solve, whose FP64
+// LDL^T factors take two registers per entry (4 blocks: at 80 registers it
+// spilled to 15 % longer steps at p = 4); FP64 at p <= 2 at 3 (their natural
+// fit); FP64 at p >= 3 needs the full register file.
+template <int P, class Real, class PR>
 constexpr int stage_min_blocks() {
-  return std::is_same<Real, float>::value ? 6 : (P <= 2 ? 3 : 1);
+  return std::is_same<Real, float>::value ? (std::is_same<PR, double>::value ? 4 : 6) : (P <= 2 ? 3 : 1);
 }
 
 template <int P, class Real, class PR, int MODE, int FEAT>
-__global__ void __launch_bounds__(128, (stage_min_blocks<P, Real>())) stage_kernel(const StageParams<Real> sp) {
+__global__ void __launch_bounds__(128, (stage_min_blocks<P, Real, PR>())) stage_kernel(const StageParams<Real> sp) {
   double lam_acc = 0.0;
   unsigned err = 0;
   double dt = 0.0;

@@ -135,8 +135,8 @@ cudaError_t static_fp32pdf(int p, const Mesh& m, double g, const double* hb64, v
 cudaError_t static_fp32pir(int p, const Mesh& m, double g, const double* hb64, void* hb, void* hbt, void* ghb,
                            void* lin, cudaStream_t s);
 
-// static bathymetry matrix of the mixed solve: ahb [K(K+1)/2][E] float pairs
-cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, float2* ahb, cudaStream_t s);
+// static bathymetry matrix of the mixed solve: ahb [K(K+1)/2][E] low parts
+cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, float* ahb, cudaStream_t s);
 
 // FP64 element-major [F][E][K] <-> context-precision SoA [F][K][E] on the device
 template <class Real>
@@ -169,6 +169,11 @@ inline Mesh make_mesh(int nx, int ny, double x0, double y0, double Lx, double Ly
   m.ndx = m.hy / m.diag;
   m.ndy = m.hx / m.diag;
   m.periodic = periodic ? 1 : 0;
+  m.fhx = float(m.hx);
+  m.fhy = float(m.hy);
+  m.fdiag = float(m.diag);
+  m.fndx = float(m.ndx);
+  m.fndy = float(m.ndy);
   return m;
 }
 cudaError_t diag_fp64(int p, const Mesh& m, const void* w, const void* hb, double det, double g, double* partial,

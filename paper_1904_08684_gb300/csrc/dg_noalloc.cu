@@ -90,7 +90,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   const size_t o_lin = o_rec + round_up((size_t)3 * NREC * E * rs);
   const bool fp64 = arith == ARITH_FP64, mixed = arith == ARITH_FP32_PIR;
   const size_t o_ahb = o_lin + (fp64 ? round_up((size_t)2 * K * K * E * rs) : 0);
-  const size_t total = o_ahb + (mixed ? round_up(sizeof(float2) * tri_size(K) * E) : 0);
+  const size_t total = o_ahb + (mixed ? round_up(sizeof(float) * ahb_words(K) * E) : 0);
   if (total > kScratchBytes) return DG_ERR_ARG;
   void* base = nullptr;
   cudaError_t e = scratch_for_current_device(&base);
@@ -110,7 +110,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
     case ARITH_FP32_PDF: e = static_fp32pdf(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
     case ARITH_FP32_PIR:
       e = static_fp32pir(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s);
-      if (e == cudaSuccess) e = static_ahb(P, m, d_hb, reinterpret_cast<float2*>(b + o_ahb), s);
+      if (e == cudaSuccess) e = static_ahb(P, m, d_hb, reinterpret_cast<float*>(b + o_ahb), s);
       break;
     default: e = static_fp32p32(P, m, cfg->g, d_hb, b + o_hb, b + o_hbt, b + o_ghb, nullptr, s); break;
   }
@@ -124,7 +124,7 @@ dg_status run(const dg_config* cfg, int arith, const double* d_hb, const void* d
   sp.hbt = reinterpret_cast<const Real*>(b + o_hbt);
   sp.ghb = reinterpret_cast<const Real*>(b + o_ghb);
   sp.lin = static_cast<const Real*>(lin);
-  sp.ahb = mixed ? reinterpret_cast<const float2*>(b + o_ahb) : nullptr;
+  sp.ahb = mixed ? reinterpret_cast<const float*>(b + o_ahb) : nullptr;
   sp.inv_det = 1.0 / (hx * hy);
   sp.det = hx * hy;
   sp.tau_bf = cfg->tau_bf;

@@ -45,7 +45,7 @@ struct dg_ctx {
   void* hbt;             // [3][PB1][E]
   void* ghb;             // [2][KB1][E]
   void* lin;             // FP64 only: [2][K][K][E] terms linear in xi
-  float2* ahb;           // mixed solve only: [K(K+1)/2][E] bathymetry matrix (float pairs)
+  float* ahb;            // mixed solve only: [ahb_words(K)][E] bathymetry matrix parts
   double* geo;           // general meshes: [NGEO][E] per-element geometry
   double* vq;            // forcing: volume Gauss rule [3][nqv]
   double* eq;            // forcing: edge Gauss rule [nqe][7]
@@ -538,7 +538,7 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   alloc(&c->hbt, (size_t)3 * c->PB1 * E * c->rsz);
   alloc(&c->ghb, (size_t)2 * c->KB1 * E * c->rsz);
   if (c->arith == ARITH_FP64) alloc(&c->lin, (size_t)2 * c->K * c->K * E * c->rsz);
-  if (c->arith == ARITH_FP32_PIR) alloc((void**)&c->ahb, sizeof(float2) * tri_size(c->K) * E);
+  if (c->arith == ARITH_FP32_PIR) alloc((void**)&c->ahb, sizeof(float) * ahb_words(c->K) * E);
   if (!geo_h.empty()) alloc((void**)&c->geo, sizeof(double) * geo_h.size());
   std::vector<double> vq_h, eq_h;
   if (cfg->forcing == DG_FORCING_MANUFACTURED) {
