@@ -198,13 +198,18 @@ dg_status dg_run(dg_ctx* ctx, int nsteps, double* t_out);
 
 /* Copy the state, the coefficients c_ei of xi, q_x, q_y (paper §2.2,
  * Eqs. (13)-(14)), to host FP64 AoS arrays [E][K] (each may be NULL; the
- * caller owns them).  Synchronises the stream.
+ * caller owns them).  Page-locked arrays mapped into the device's address
+ * space (cudaHostAlloc, cudaHostRegister; both ends of each array checked)
+ * are written in place by one conversion kernel over the host link; other
+ * arrays receive copies from a device staging buffer (allocated on first
+ * use).  Synchronises the stream.
  * Errors: DG_ERR_ARG, DG_ERR_OOM (staging buffer), DG_ERR_CUDA. */
 dg_status dg_get_state(dg_ctx* ctx, double* xi, double* qx, double* qy);
 
 /* Replace the state (coefficients of Eqs. (13)-(14), host FP64 AoS [E][K],
- * all three required, copied) and the time t.  The next step re-evaluates
- * the new state.  Synchronises the stream.
+ * all three required, copied; mapped page-locked arrays are read in place
+ * as at dg_get_state) and the time t.  The next step re-evaluates the new
+ * state.  Synchronises the stream.
  * Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_CUDA. */
 dg_status dg_set_state(dg_ctx* ctx, const double* xi, const double* qx, const double* qy, double t);
 
@@ -316,9 +321,10 @@ dg_status dg_batch_init_device(int n, const dg_config* cfgs, const void* const* 
 dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out);
 
 /* state of instance i (coefficients of Eqs. (13)-(14)) as host FP64 AoS
- * [E_i][K_i] arrays (each may be NULL; page-locked buffers make the copies
- * faster).  Synchronises the stream (the first call allocates the staging
- * area described at dg_batch_set_state).  Errors: DG_ERR_ARG, DG_ERR_OOM,
+ * [E_i][K_i] arrays (each may be NULL).  Mapped page-locked arrays are
+ * written in place by one conversion kernel (as dg_get_state); others are
+ * copied from the staging area described at dg_batch_set_state (allocated
+ * by the first such call).  Synchronises the stream.  Errors: DG_ERR_ARG, DG_ERR_OOM,
  * DG_ERR_CUDA. */
 dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy);
 
@@ -327,9 +333,10 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
  * dg_batch_run re-evaluates the batch.  Asynchronous on the batch's stream
  * (the copies of successive calls overlap): the arrays must stay unchanged
  * until the stream is synchronised -- dg_batch_run, dg_batch_get_state and
- * every other synchronising call do; page-locked arrays copy fastest.  The
- * first call allocates a device staging area for every instance's FP64
- * state (kept until dg_batch_destroy).  Errors: DG_ERR_ARG, DG_ERR_OOM,
+ * every other synchronising call do.  Mapped page-locked arrays are read in
+ * place by one conversion kernel (as dg_get_state); for other arrays the
+ * first such call allocates a device staging area for every instance's
+ * FP64 state (kept until dg_batch_destroy).  Errors: DG_ERR_ARG, DG_ERR_OOM,
  * DG_ERR_CUDA. */
 dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double* qx, const double* qy, double t);
 

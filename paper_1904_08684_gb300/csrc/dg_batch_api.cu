@@ -677,18 +677,30 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
   if (!b || i < 0 || i >= b->n) return DG_ERR_ARG;
   const HostInst& h = b->inst[i];
   const long long E = h.E, KE = (long long)h.K * E;
+  const char* src = (const char*)b->w[0] + h.o_state;
+  double* dst[3] = {xi, qx, qy};
+  HostFields hf;
+  if (mapped_fields(dst, KE, hf)) {
+    // page-locked, mapped host arrays: written in place by one kernel
+    const unsigned gf = fields_grid(E, h.K);
+    if (b->arith == ARITH_FP64)
+      soa_to_fields_kernel<double><<<gf, 256, 0, b->stream>>>((const double*)src, hf, E, h.K);
+    else
+      soa_to_fields_kernel<float><<<gf, 256, 0, b->stream>>>((const float*)src, hf, E, h.K);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(b->stream));
+    return DG_OK;
+  }
   dg_status s = ensure_batch_stage(b, b->stage_total);
   if (s != DG_OK) return s;
   double* slice = b->stage + h.o_stage;
   // device transpose to element-major FP64, then one copy per field
-  const char* src = (const char*)b->w[0] + h.o_state;
   const unsigned g = (unsigned)((E + 127) / 128);
   if (b->arith == ARITH_FP64)
     soa_to_aos_kernel<double><<<g, 128, 0, b->stream>>>((const double*)src, slice, E, h.K, 3);
   else
     soa_to_aos_kernel<float><<<g, 128, 0, b->stream>>>((const float*)src, slice, E, h.K, 3);
   CK(cudaGetLastError());
-  double* dst[3] = {xi, qx, qy};
   for (int f = 0; f < 3; ++f)
     if (dst[f])
       CK(cudaMemcpyAsync(dst[f], slice + (size_t)f * KE, sizeof(double) * KE, cudaMemcpyDeviceToHost, b->stream));
@@ -701,21 +713,32 @@ dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double*
   if (!b || i < 0 || i >= b->n || !xi || !qx || !qy) return DG_ERR_ARG;
   const HostInst& h = b->inst[i];
   const long long E = h.E, KE = (long long)h.K * E;
-  dg_status s = ensure_batch_stage(b, b->stage_total);
-  if (s != DG_OK) return s;
-  double* slice = b->stage + h.o_stage;
-  // asynchronous: the copies of different instances go to different slices
-  // and overlap; the caller keeps its arrays unchanged until the stream is
-  // synchronised (dg_batch_run does)
-  const double* src[3] = {xi, qx, qy};
-  for (int f = 0; f < 3; ++f)
-    CK(cudaMemcpyAsync(slice + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, b->stream));
+  // asynchronous: the caller keeps its arrays unchanged until the stream is
+  // synchronised (dg_batch_run does).  Page-locked, mapped host arrays are
+  // read in place by one kernel; others are copied into this instance's
+  // staging slice (the copies of different instances overlap) and
+  // transposed on the device.
+  double* src[3] = {const_cast<double*>(xi), const_cast<double*>(qx), const_cast<double*>(qy)};
   char* dst = (char*)b->w[0] + h.o_state;
-  const unsigned g = (unsigned)((E + 127) / 128);
-  if (b->arith == ARITH_FP64)
-    aos_to_soa_kernel<double><<<g, 128, 0, b->stream>>>(slice, (double*)dst, E, h.K, 3);
-  else
-    aos_to_soa_kernel<float><<<g, 128, 0, b->stream>>>(slice, (float*)dst, E, h.K, 3);
+  HostFields hf;
+  if (mapped_fields(src, KE, hf)) {
+    const unsigned gf = fields_grid(E, h.K);
+    if (b->arith == ARITH_FP64)
+      fields_to_soa_kernel<double><<<gf, 256, 0, b->stream>>>(hf, (double*)dst, E, h.K);
+    else
+      fields_to_soa_kernel<float><<<gf, 256, 0, b->stream>>>(hf, (float*)dst, E, h.K);
+  } else {
+    dg_status s = ensure_batch_stage(b, b->stage_total);
+    if (s != DG_OK) return s;
+    double* slice = b->stage + h.o_stage;
+    for (int f = 0; f < 3; ++f)
+      CK(cudaMemcpyAsync(slice + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, b->stream));
+    const unsigned g = (unsigned)((E + 127) / 128);
+    if (b->arith == ARITH_FP64)
+      aos_to_soa_kernel<double><<<g, 128, 0, b->stream>>>(slice, (double*)dst, E, h.K, 3);
+    else
+      aos_to_soa_kernel<float><<<g, 128, 0, b->stream>>>(slice, (float*)dst, E, h.K, 3);
+  }
   CK(cudaGetLastError());
   set_scalar_kernel<<<1, 1, 0, b->stream>>>(b->t + i, t);   // t by value: no host memory outlives the call
   CK(cudaGetLastError());

@@ -154,6 +154,79 @@ __global__ void soa_to_aos_kernel(const Real* __restrict__ b, double* __restrict
     for (int i = 0; i < K; ++i) a[((long long)f * E + e) * K + i] = double(b[((long long)f * K + i) * E + e]);
 }
 
+// Three element-major FP64 arrays [E][K] (xi, q_x, q_y) that the device reads
+// or writes directly in host memory (page-locked and mapped), <-> the
+// context-precision SoA state [3][K][E].  One thread per host word, in the
+// host arrays' order, so that the traffic over the host link is coalesced
+// (the device side, scattered by K rows, merges in L2).  A null field is
+// skipped.
+struct HostFields {
+  double* f[3];
+};
+template <class Real>
+__global__ void __launch_bounds__(256) fields_to_soa_kernel(HostFields a, Real* __restrict__ b, long long E, int K) {
+  const long long n = E * K;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < 3 * n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(idx / n);
+    const long long r = idx - f * n, e = r / K;
+    const int i = (int)(r - e * K);
+    if (a.f[f]) b[((long long)f * K + i) * E + e] = Real(a.f[f][r]);
+  }
+}
+template <class Real>
+__global__ void __launch_bounds__(256) soa_to_fields_kernel(const Real* __restrict__ b, HostFields a, long long E,
+                                                           int K) {
+  const long long n = E * K;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < 3 * n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int f = (int)(idx / n);
+    const long long r = idx - f * n, e = r / K;
+    const int i = (int)(r - e * K);
+    if (a.f[f]) a.f[f][r] = double(b[((long long)f * K + i) * E + e]);
+  }
+}
+inline unsigned fields_grid(long long E, int K) {
+  const long long blocks = (3 * E * K + 255) / 256;
+  return (unsigned)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096);
+}
+
+// Device address of a host array of `bytes` bytes that kernels may access in
+// place: page-locked memory mapped into the device's address space
+// (cudaHostAlloc, cudaHostRegister), checked at its first and last byte;
+// null for any other memory (pageable arrays go through copies instead).
+inline double* mapped_host(const double* p, size_t bytes) {
+  if (!p || bytes == 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const char* last = (const char*)p + bytes - 1;
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+    return nullptr;
+  if ((const char*)a1.devicePointer - (const char*)a0.devicePointer != (long long)bytes - 1) return nullptr;
+  return (double*)a0.devicePointer;
+}
+
+// The three fields' device addresses (n doubles each; null stays null) when
+// every non-null field is mapped host memory and at least one is given
+inline bool mapped_fields(double* const* p, long long n, HostFields& hf) {
+  bool any = false;
+  for (int f = 0; f < 3; ++f) {
+    hf.f[f] = nullptr;
+    if (!p[f]) continue;
+    hf.f[f] = mapped_host(p[f], sizeof(double) * (size_t)n);
+    if (!hf.f[f]) return false;
+    any = true;
+  }
+  return any;
+}
+
 // fill the derived geometry of a uniform mesh
 inline Mesh make_mesh(int nx, int ny, double x0, double y0, double Lx, double Ly, bool periodic) {
   Mesh m;

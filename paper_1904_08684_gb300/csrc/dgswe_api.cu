@@ -745,10 +745,11 @@ dg_status dg_state_device(dg_ctx* c, void** d_state) {
   return DG_OK;
 }
 
-// Host copies of the state go through a device staging buffer (allocated on
-// first use, kept with the context): the caller's element-major arrays are
-// copied as they are (asynchronously; page-locked arrays copy fastest) and
-// transposed on the device.
+// Host state arrays that are page-locked and mapped are read or written in
+// place by one conversion kernel (over the host link, no copy engine and no
+// staging buffer).  Other host arrays go through a device staging buffer
+// (allocated on first use, kept with the context): the caller's
+// element-major arrays are copied as they are and transposed on the device.
 static dg_status ensure_stage(dg_ctx* c) {
   if (!c->stage) CK(cudaMalloc((void**)&c->stage, sizeof(double) * 3 * (size_t)c->K * c->E));
   return DG_OK;
@@ -757,16 +758,27 @@ static dg_status ensure_stage(dg_ctx* c) {
 dg_status dg_get_state(dg_ctx* c, double* xi, double* qx, double* qy) {
   dgswe::NvtxRange nvtx_range("dg_get_state");
   if (!c) return DG_ERR_ARG;
+  const long long E = c->E, KE = (long long)c->K * E;
+  double* dst[3] = {xi, qx, qy};
+  dgswe::HostFields hf;
+  if (mapped_fields(dst, KE, hf)) {
+    const unsigned gf = dgswe::fields_grid(E, c->K);
+    if (c->arith == ARITH_FP64)
+      dgswe::soa_to_fields_kernel<double><<<gf, 256, 0, c->stream>>>((const double*)c->w[0], hf, E, c->K);
+    else
+      dgswe::soa_to_fields_kernel<float><<<gf, 256, 0, c->stream>>>((const float*)c->w[0], hf, E, c->K);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    return DG_OK;
+  }
   dg_status s = ensure_stage(c);
   if (s != DG_OK) return s;
-  const long long E = c->E, KE = (long long)c->K * E;
   const unsigned g = (unsigned)((E + 127) / 128);
   if (c->arith == ARITH_FP64)
     soa_to_aos_kernel<double><<<g, 128, 0, c->stream>>>((const double*)c->w[0], c->stage, E, c->K, 3);
   else
     soa_to_aos_kernel<float><<<g, 128, 0, c->stream>>>((const float*)c->w[0], c->stage, E, c->K, 3);
   CK(cudaGetLastError());
-  double* dst[3] = {xi, qx, qy};
   for (int f = 0; f < 3; ++f)
     if (dst[f])
       CK(cudaMemcpyAsync(dst[f], c->stage + (size_t)f * KE, sizeof(double) * KE, cudaMemcpyDeviceToHost, c->stream));
@@ -777,17 +789,26 @@ dg_status dg_get_state(dg_ctx* c, double* xi, double* qx, double* qy) {
 dg_status dg_set_state(dg_ctx* c, const double* xi, const double* qx, const double* qy, double t) {
   dgswe::NvtxRange nvtx_range("dg_set_state");
   if (!c || !xi || !qx || !qy) return DG_ERR_ARG;
-  dg_status s = ensure_stage(c);
-  if (s != DG_OK) return s;
   const long long E = c->E, KE = (long long)c->K * E;
-  const double* src[3] = {xi, qx, qy};
-  for (int f = 0; f < 3; ++f)
-    CK(cudaMemcpyAsync(c->stage + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, c->stream));
-  const unsigned g = (unsigned)((E + 127) / 128);
-  if (c->arith == ARITH_FP64)
-    aos_to_soa_kernel<double><<<g, 128, 0, c->stream>>>(c->stage, (double*)c->w[0], E, c->K, 3);
-  else
-    aos_to_soa_kernel<float><<<g, 128, 0, c->stream>>>(c->stage, (float*)c->w[0], E, c->K, 3);
+  double* src[3] = {const_cast<double*>(xi), const_cast<double*>(qx), const_cast<double*>(qy)};
+  dgswe::HostFields hf;
+  if (mapped_fields(src, KE, hf)) {
+    const unsigned gf = dgswe::fields_grid(E, c->K);
+    if (c->arith == ARITH_FP64)
+      dgswe::fields_to_soa_kernel<double><<<gf, 256, 0, c->stream>>>(hf, (double*)c->w[0], E, c->K);
+    else
+      dgswe::fields_to_soa_kernel<float><<<gf, 256, 0, c->stream>>>(hf, (float*)c->w[0], E, c->K);
+  } else {
+    dg_status s = ensure_stage(c);
+    if (s != DG_OK) return s;
+    for (int f = 0; f < 3; ++f)
+      CK(cudaMemcpyAsync(c->stage + (size_t)f * KE, src[f], sizeof(double) * KE, cudaMemcpyHostToDevice, c->stream));
+    const unsigned g = (unsigned)((E + 127) / 128);
+    if (c->arith == ARITH_FP64)
+      aos_to_soa_kernel<double><<<g, 128, 0, c->stream>>>(c->stage, (double*)c->w[0], E, c->K, 3);
+    else
+      aos_to_soa_kernel<float><<<g, 128, 0, c->stream>>>(c->stage, (float*)c->w[0], E, c->K, 3);
+  }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(c->scal + 2, &t, sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));

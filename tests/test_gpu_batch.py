@@ -95,6 +95,38 @@ def test_batch_set_state_resumes_bit_exactly():
         B.dg_batch_destroy(b2)
 
 
+def test_batch_state_through_page_locked_host_arrays():
+    """dg_batch_get_state / dg_batch_set_state with page-locked host arrays
+    (in place, one conversion kernel each) agree bit for bit with pageable
+    arrays (staged copies), FP32 and FP64 batches"""
+    for precision in ("fp32", "fp64"):
+        inst = [_instance(k, *s, precision) for k, s in enumerate(SPECS)]
+        args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
+                [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
+        b1 = B.dg_batch_init_device(*args)
+        b2 = B.dg_batch_init_device(*args)
+        try:
+            t4 = B.dg_batch_run(b1, 4)
+            pinned = []
+            for i, (_, _, E, K) in enumerate(inst):
+                ref = B.dg_batch_get_state(b1, i, E, K)
+                pv = [torch.full((E, K), float("nan"), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+                B.dg_batch_get_state(b1, i, E, K, out=pv)
+                for a, r in zip(pv, ref):
+                    assert np.array_equal(a, r), (precision, i)
+                pinned.append(pv)
+                B.dg_batch_set_state(b2, i, *pv, t=float(t4[i]))
+            t1 = B.dg_batch_run(b1, 3)
+            t2 = B.dg_batch_run(b2, 3)
+            assert np.array_equal(t1, t2)
+            for i, (_, _, E, K) in enumerate(inst):
+                for a, r in zip(B.dg_batch_get_state(b2, i, E, K, out=pinned[i]), B.dg_batch_get_state(b1, i, E, K)):
+                    assert np.array_equal(a, r), (precision, i)
+        finally:
+            B.dg_batch_destroy(b1)
+            B.dg_batch_destroy(b2)
+
+
 @pytest.mark.parametrize("tile", [1, -1])
 def test_batch_autotune_keeps_state(tile):
     """the autotuner (tile shapes of a tile-fused batch, elements per work

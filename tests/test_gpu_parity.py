@@ -353,6 +353,52 @@ def test_deterministic_and_checkpoint_resume(oracle_mod):
         assert np.array_equal(a, b)
 
 
+def _pinned_views(E, K, n=3, offset=5):
+    """n (E, K) float64 arrays inside one page-locked buffer, the first
+    starting ``offset`` words in (an interior pointer of the allocation)"""
+    buf = torch.empty(offset + n * E * K + 7, dtype=torch.float64).pin_memory().numpy()
+    buf[:] = np.nan
+    return buf, [buf[offset + k * E * K: offset + (k + 1) * E * K].reshape(E, K) for k in range(n)]
+
+
+@pytest.mark.parametrize("precision,proj", [("fp64", "fp64"), ("fp32", "mixed")])
+def test_state_through_page_locked_host_arrays(oracle_mod, precision, proj):
+    """dg_get_state / dg_set_state with page-locked arrays (read and written
+    in place by the conversion kernels over the host link) give the bits of
+    pageable arrays (staged copies), on a ragged 13 x 11 mesh; the words
+    around the arrays stay untouched; a run continued from a state set
+    through page-locked arrays equals one continued from pageable arrays."""
+    wl = I.waves_p2_512(n=13, p=2, ngauss=3)
+    wl.ny = 11
+    o = oracle_mod.Oracle(13, 11, 2, bc="periodic")
+    hb, xi, U, V = _state(o, wl)
+    cfg = _cfg(wl, precision=precision, proj_precision=proj)
+    E, K = o.E, o.K
+    ctx = B.dg_init(cfg, hb, xi, U, V)
+    try:
+        t = B.dg_run(ctx, 7)
+        ref = B.dg_get_state(ctx, E, K)
+        buf, views = _pinned_views(E, K)
+        B.dg_get_state(ctx, E, K, out=views)
+        for a, r in zip(views, ref):
+            assert np.array_equal(a, r)
+        assert np.isnan(buf[:5]).all() and np.isnan(buf[5 + 3 * E * K:]).all()
+        # a perturbed state set through each kind of array, then 3 steps
+        new = [r * (1.0 + 1e-3 * np.cos(np.arange(r.size)).reshape(r.shape)) for r in ref]
+        B.dg_set_state(ctx, *new, t=t)
+        B.dg_run(ctx, 3)
+        want = B.dg_get_state(ctx, E, K)
+        for v, a in zip(views, new):
+            v[:] = a
+        B.dg_set_state(ctx, *views, t=t)
+        B.dg_run(ctx, 3)
+        got = B.dg_get_state(ctx, E, K, out=_pinned_views(E, K, offset=0)[1])
+        for a, r in zip(got, want):
+            assert np.array_equal(a, r)
+    finally:
+        B.dg_destroy(ctx)
+
+
 def test_diagnostics_match_oracle(oracle_mod):
     wl = I.waves_p2_512(n=10, p=2, ngauss=3)
     o = oracle_mod.Oracle(10, 10, 2, bc="periodic")
