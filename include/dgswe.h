@@ -328,6 +328,15 @@ dg_status dg_batch_run(dg_batch* b, int nsteps, double* t_out);
  * DG_ERR_CUDA. */
 dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy);
 
+/* every instance's state (coefficients of Eqs. (13)-(14)) at once: xi[i],
+ * qx[i], qy[i] as for dg_batch_get_state(b, i, ...) (host arrays of
+ * n_instances pointers; the caller owns them and the arrays they point to;
+ * any entry may be NULL), the transfers of all instances enqueued back to
+ * back and the stream synchronised once.
+ * Errors as dg_batch_get_state (DG_ERR_ARG also for a NULL pointer array);
+ * on an error some instances may have been written. */
+dg_status dg_batch_get_states(dg_batch* b, double* const* xi, double* const* qx, double* const* qy);
+
 /* replace the state of instance i (coefficients of Eqs. (13)-(14), host FP64
  * AoS [E_i][K_i] arrays, all three required) and its model time t; the next
  * dg_batch_run re-evaluates the batch.  Asynchronous on the batch's stream

@@ -26,7 +26,8 @@ PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
 EXPORTS = ["dg_num_basis", "dg_num_basis_bathymetry", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
            "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc",
-           "dg_batch_init", "dg_batch_init_device", "dg_batch_run", "dg_batch_get_state", "dg_batch_set_state", "dg_batch_autotune",
+           "dg_batch_init", "dg_batch_init_device", "dg_batch_run", "dg_batch_get_state", "dg_batch_get_states", "dg_batch_set_state",
+           "dg_batch_autotune",
            "dg_batch_set_block", "dg_batch_tile_shape", "dg_batch_dofs", "dg_batch_destroy"]
 
 
@@ -110,6 +111,7 @@ def load(build_if_missing=True):
     lib.dg_batch_init_device.argtypes = [ctypes.c_int, cp, vpp, vpp, vpp, vpp, vp, ctypes.POINTER(vp)]
     lib.dg_batch_run.argtypes = [vp, ctypes.c_int, dp]
     lib.dg_batch_get_state.argtypes = [vp, ctypes.c_int, dp, dp, dp]
+    lib.dg_batch_get_states.argtypes = [vp, dpp, dpp, dpp]
     lib.dg_batch_set_state.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_double]
     lib.dg_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
     lib.dg_batch_set_block.argtypes = [vp, ctypes.c_int]
@@ -320,6 +322,24 @@ def dg_batch_get_state(b, i, E, K, out=None):
     for a in out:
         assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == E * K
     _check(load().dg_batch_get_state(b, int(i), *[_hptr(a) for a in out]), "dg_batch_get_state")
+    return out
+
+
+def dg_batch_get_states(b, shapes, out=None):
+    """every instance's state (one synchronisation): shapes = [(E_i, K_i)];
+    returns [[xi, qx, qy] per instance] as host (E_i, K_i) FP64 arrays
+    (written into ``out`` if given, e.g. page-locked buffers)"""
+    n = len(shapes)
+    if out is None:
+        out = [[np.zeros((E, K)) for _ in range(3)] for E, K in shapes]
+    if len(out) != n:
+        raise ValueError("expected %d instances, got %d" % (n, len(out)))
+    ptrs = [(ctypes.POINTER(ctypes.c_double) * n)() for _ in range(3)]
+    for i, ((E, K), arrs) in enumerate(zip(shapes, out)):
+        for f, a in enumerate(arrs):
+            assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == E * K
+            ptrs[f][i] = _hptr(a)
+    _check(load().dg_batch_get_states(b, *ptrs), "dg_batch_get_states")
     return out
 
 

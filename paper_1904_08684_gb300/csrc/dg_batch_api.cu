@@ -672,9 +672,10 @@ static dg_status ensure_batch_stage(dg_batch* b, size_t doubles) {
   return DG_OK;
 }
 
-dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy) {
-  dgswe::NvtxRange nvtx_range("dg_batch_get_state");
-  if (!b || i < 0 || i >= b->n) return DG_ERR_ARG;
+// Enqueue the transfer of instance i's state to host arrays (no
+// synchronisation): in place for mapped page-locked arrays, else through the
+// instance's staging slice.
+static dg_status enqueue_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy) {
   const HostInst& h = b->inst[i];
   const long long E = h.E, KE = (long long)h.K * E;
   const char* src = (const char*)b->w[0] + h.o_state;
@@ -688,7 +689,6 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
     else
       soa_to_fields_kernel<float><<<gf, 256, 0, b->stream>>>((const float*)src, hf, E, h.K);
     CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(b->stream));
     return DG_OK;
   }
   dg_status s = ensure_batch_stage(b, b->stage_total);
@@ -704,6 +704,25 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
   for (int f = 0; f < 3; ++f)
     if (dst[f])
       CK(cudaMemcpyAsync(dst[f], slice + (size_t)f * KE, sizeof(double) * KE, cudaMemcpyDeviceToHost, b->stream));
+  return DG_OK;
+}
+
+dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double* qy) {
+  dgswe::NvtxRange nvtx_range("dg_batch_get_state");
+  if (!b || i < 0 || i >= b->n) return DG_ERR_ARG;
+  dg_status s = enqueue_get_state(b, i, xi, qx, qy);
+  if (s != DG_OK) return s;
+  CK(cudaStreamSynchronize(b->stream));
+  return DG_OK;
+}
+
+dg_status dg_batch_get_states(dg_batch* b, double* const* xi, double* const* qx, double* const* qy) {
+  dgswe::NvtxRange nvtx_range("dg_batch_get_states");
+  if (!b || !xi || !qx || !qy) return DG_ERR_ARG;
+  for (int i = 0; i < b->n; ++i) {
+    dg_status s = enqueue_get_state(b, i, xi[i], qx[i], qy[i]);
+    if (s != DG_OK) return s;
+  }
   CK(cudaStreamSynchronize(b->stream));
   return DG_OK;
 }

@@ -98,7 +98,8 @@ def test_batch_set_state_resumes_bit_exactly():
 def test_batch_state_through_page_locked_host_arrays():
     """dg_batch_get_state / dg_batch_set_state with page-locked host arrays
     (in place, one conversion kernel each) agree bit for bit with pageable
-    arrays (staged copies), FP32 and FP64 batches"""
+    arrays (staged copies), FP32 and FP64 batches; dg_batch_get_states
+    (all instances, one synchronisation) returns the same bits"""
     for precision in ("fp32", "fp64"):
         inst = [_instance(k, *s, precision) for k, s in enumerate(SPECS)]
         args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
@@ -119,9 +120,12 @@ def test_batch_state_through_page_locked_host_arrays():
             t1 = B.dg_batch_run(b1, 3)
             t2 = B.dg_batch_run(b2, 3)
             assert np.array_equal(t1, t2)
-            for i, (_, _, E, K) in enumerate(inst):
-                for a, r in zip(B.dg_batch_get_state(b2, i, E, K, out=pinned[i]), B.dg_batch_get_state(b1, i, E, K)):
-                    assert np.array_equal(a, r), (precision, i)
+            shapes = [(E, K) for _, _, E, K in inst]
+            # every instance at once, into page-locked and into pageable arrays
+            for got in (B.dg_batch_get_states(b2, shapes, out=pinned), B.dg_batch_get_states(b2, shapes)):
+                for i, (_, _, E, K) in enumerate(inst):
+                    for a, r in zip(got[i], B.dg_batch_get_state(b1, i, E, K)):
+                        assert np.array_equal(a, r), (precision, i)
         finally:
             B.dg_batch_destroy(b1)
             B.dg_batch_destroy(b2)
