@@ -337,6 +337,25 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
  * on an error some instances may have been written. */
 dg_status dg_batch_get_states(dg_batch* b, double* const* xi, double* const* qx, double* const* qy);
 
+/* One SSP-RK step (reading R6) of every instance from host states to host
+ * states, as dg_batch_set_state(b, i, xi_in[i], qx_in[i], qy_in[i], t_i)
+ * for every i (t_i its current time), dg_batch_run(b, 1, t_out) and
+ * dg_batch_get_states(b, xi_out, qx_out, qy_out) would do, with the same
+ * bits: host FP64 AoS [E_i][K_i] arrays behind arrays of n_instances
+ * pointers (none NULL; the caller owns all; out may alias in).  Pipelined
+ * (tile-fused batches; one group otherwise): every order class is cut into
+ * runs of consecutive instances of about 1/16 of the batch's state bytes;
+ * a run's state goes up by copy engine into the staging area (allocated on
+ * first use, as at dg_batch_set_state), is evaluated and advanced by its
+ * own stage launches and comes back by copy engine, while later runs go up
+ * and earlier ones come down; page-locked arrays copy fastest.
+ * Synchronises the stream.  t_out (n_instances doubles) may be NULL.
+ * Errors: DG_ERR_ARG, DG_ERR_OOM, DG_ERR_DRY, DG_ERR_NONFINITE (as
+ * dg_batch_run: the step was taken and the word cleared), DG_ERR_CUDA. */
+dg_status dg_batch_step_host(dg_batch* b, const double* const* xi_in, const double* const* qx_in,
+                             const double* const* qy_in, double* const* xi_out, double* const* qx_out,
+                             double* const* qy_out, double* t_out);
+
 /* replace the state of instance i (coefficients of Eqs. (13)-(14), host FP64
  * AoS [E_i][K_i] arrays, all three required) and its model time t; the next
  * dg_batch_run re-evaluates the batch.  Asynchronous on the batch's stream

@@ -26,7 +26,7 @@ PREC = {"fp64": DG_PREC_FP64, "fp32": DG_PREC_FP32_MIXED}
 EXPORTS = ["dg_num_basis", "dg_num_basis_bathymetry", "dg_num_elements", "dg_init", "dg_init_device", "dg_rhs", "dg_rk_step", "dg_run",
            "dg_get_state", "dg_set_state", "dg_state_device", "dg_diagnostics", "dg_proj_num_nodes",
            "dg_proj_nodes", "dg_project", "dg_destroy", "dg_status_str", "dg_rhs_noalloc",
-           "dg_batch_init", "dg_batch_init_device", "dg_batch_run", "dg_batch_get_state", "dg_batch_get_states", "dg_batch_set_state",
+           "dg_batch_init", "dg_batch_init_device", "dg_batch_run", "dg_batch_get_state", "dg_batch_get_states", "dg_batch_set_state", "dg_batch_step_host",
            "dg_batch_autotune",
            "dg_batch_set_block", "dg_batch_tile_shape", "dg_batch_dofs", "dg_batch_destroy"]
 
@@ -112,6 +112,7 @@ def load(build_if_missing=True):
     lib.dg_batch_run.argtypes = [vp, ctypes.c_int, dp]
     lib.dg_batch_get_state.argtypes = [vp, ctypes.c_int, dp, dp, dp]
     lib.dg_batch_get_states.argtypes = [vp, dpp, dpp, dpp]
+    lib.dg_batch_step_host.argtypes = [vp, dpp, dpp, dpp, dpp, dpp, dpp, dp]
     lib.dg_batch_set_state.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_double]
     lib.dg_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
     lib.dg_batch_set_block.argtypes = [vp, ctypes.c_int]
@@ -341,6 +342,31 @@ def dg_batch_get_states(b, shapes, out=None):
             ptrs[f][i] = _hptr(a)
     _check(load().dg_batch_get_states(b, *ptrs), "dg_batch_get_states")
     return out
+
+
+def dg_batch_step_host(b, shapes, states, out=None):
+    """one step of every instance from host states to host states:
+    states = [[xi, qx, qy] per instance] (host (E_i, K_i) FP64 arrays);
+    returns (out, t) with out in the same form (``states`` itself may be
+    passed as ``out``) and t the instances' times after the step"""
+    n = len(shapes)
+    if out is None:
+        out = [[np.zeros((E, K)) for _ in range(3)] for E, K in shapes]
+    if len(states) != n or len(out) != n:
+        raise ValueError("expected %d instances" % n)
+    ptrs = [(ctypes.POINTER(ctypes.c_double) * n)() for _ in range(6)]
+    keep = []
+    for i, (E, K) in enumerate(shapes):
+        for f in range(3):
+            a = _host(states[i][f], E, K)
+            keep.append(a)
+            ptrs[f][i] = _hptr(a)
+            o = out[i][f]
+            assert o.dtype == np.float64 and o.flags.c_contiguous and o.size == E * K
+            ptrs[3 + f][i] = _hptr(o)
+    t = np.zeros(n)
+    _check(load().dg_batch_step_host(b, *ptrs, _hptr(t)), "dg_batch_step_host")
+    return out, t
 
 
 def dg_batch_set_state(b, i, xi, qx, qy, t=0.0):

@@ -89,22 +89,34 @@ struct dg_batch {
   int ep = 0, lc = 0;
   bool evaluated = false;
   cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+  std::vector<int> item_lo, item_hi;  // per instance: its work items [lo, hi)
+  // dg_batch_step_host: copy streams, events and per-group work counters
+  // (created on first use)
+  cudaStream_t s_up = nullptr, s_down = nullptr;
+  std::vector<cudaEvent_t> ev_up, ev_done;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  unsigned* pcount = nullptr;         // [groups][S]
   long long dofs = 0;
 };
 
 namespace {
 
-// tile-fused launch of order class p (items [cls_begin[p], cls_end[p]))
-cudaError_t launch_tile_class(const dg_batch* b, int p, BatchArgs a, cudaStream_t s) {
-  a.item_begin = b->cls_begin[p];
-  a.n_items = b->cls_end[p];
-  const int shape = b->cls_shape[p], grid = b->cls_grid[p];
+// tile-fused launch of items [lo, hi) of order class p on `grid` CTAs
+cudaError_t launch_tile_range(const dg_batch* b, int p, int lo, int hi, int grid, BatchArgs a, cudaStream_t s) {
+  a.item_begin = lo;
+  a.n_items = hi;
+  const int shape = b->cls_shape[p];
   switch (b->arith) {
     case ARITH_FP32_P64: return batch_tile_launch_fp32p64(p, shape, grid, a, s);
     case ARITH_FP32_PDF: return batch_tile_launch_fp32pdf(p, shape, grid, a, s);
     case ARITH_FP32_PIR: return batch_tile_launch_fp32pir(p, shape, grid, a, s);
     default: return batch_tile_launch_fp32p32(p, shape, grid, a, s);
   }
+}
+
+// tile-fused launch of order class p (items [cls_begin[p], cls_end[p]))
+cudaError_t launch_tile_class(const dg_batch* b, int p, const BatchArgs& a, cudaStream_t s) {
+  return launch_tile_range(b, p, b->cls_begin[p], b->cls_end[p], b->cls_grid[p], a, s);
 }
 
 cudaError_t launch_batch(const dg_batch* b, int mode, const BatchArgs& a, cudaStream_t s) {
@@ -128,26 +140,30 @@ BatchArgs base_args(const dg_batch* b) {
   return a;
 }
 
+// CFL maximum of instance i's current state into its slot of lam row lc
+// (tile-fused batches; the slot zeroed by the caller)
+cudaError_t launch_wave_speed(const dg_batch* b, int i, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const HostInst& h = b->inst[i];
+  long long g = (h.E + 255) / 256;
+  if (g > 4LL * sms) g = 4LL * sms;
+  const Mesh m = make_mesh(h.cfg.nx, h.cfg.ny, h.cfg.x0, h.cfg.y0, h.cfg.Lx, h.cfg.Ly, h.cfg.bc == DG_BC_PERIODIC);
+  wave_speed_kernel<float><<<(unsigned)g, 256, 0, s>>>(m, float(h.cfg.g), h.K, (const float*)((char*)b->w[0] + h.o_state),
+                                                       (const float*)((char*)b->hb + h.o_hb),
+                                                       b->lam + (size_t)b->lc * b->n + i);
+  return cudaGetLastError();
+}
+
 dg_status launch_eval(dg_batch* b, cudaStream_t s) {
   CK(cudaMemsetAsync(b->counters, 0, sizeof(unsigned), s));
   CK(cudaMemsetAsync(b->lam + (size_t)b->lc * b->n, 0, sizeof(double) * b->n, s));
   if (b->tiled) {
     // the tile-fused stages evaluate their own input: only the first step's
     // CFL maximum of every instance is needed
-    int dev = 0, sms = 0;
-    CK(cudaGetDevice(&dev));
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    for (int i = 0; i < b->n; ++i) {
-      const HostInst& h = b->inst[i];
-      long long g = (h.E + 255) / 256;
-      if (g > 4LL * sms) g = 4LL * sms;
-      const Mesh m = make_mesh(h.cfg.nx, h.cfg.ny, h.cfg.x0, h.cfg.y0, h.cfg.Lx, h.cfg.Ly,
-                               h.cfg.bc == DG_BC_PERIODIC);
-      wave_speed_kernel<float><<<(unsigned)g, 256, 0, s>>>(m, float(h.cfg.g), h.K, (const float*)((char*)b->w[0] + h.o_state),
-                                                           (const float*)((char*)b->hb + h.o_hb),
-                                                           b->lam + (size_t)b->lc * b->n + i);
-      CK(cudaGetLastError());
-    }
+    for (int i = 0; i < b->n; ++i) CK(launch_wave_speed(b, i, s));
     return DG_OK;
   }
   BatchArgs a = base_args(b);
@@ -208,6 +224,30 @@ dg_status launch_step(const dg_batch* b, int ep, int lc, cudaStream_t s, double*
   return st_out;
 }
 
+// The stages of one step for the items [lo, hi) of order class p alone
+// (tile-fused batches; whole instances): the class launches of launch_step
+// restricted to those instances.  The instances are independent, so
+// stepping groups of them one after another instead of stage by stage gives
+// the same bits.  counters: one per stage, zeroed by the caller (with the
+// next step's CFL row when adaptive) before the first group.
+dg_status launch_range_step(const dg_batch* b, int p, int lo, int hi, unsigned* counters, int ep, int lc,
+                            cudaStream_t s) {
+  const int grid = std::max(1, std::min(b->cls_grid[p], hi - lo));
+  for (int st = 0; st < b->S; ++st) {
+    BatchArgs a = base_args(b);
+    a.win = st == 0 ? 0 : st;
+    a.wout = st == b->S - 1 ? 0 : st + 1;
+    a.pin = (ep + st) & 1;
+    a.beta = RK_B[b->S - 1][st];
+    a.alpha = 1.0 - a.beta;
+    a.lc = lc;
+    a.last = st == b->S - 1;
+    a.counter = counters + st;
+    CK(launch_tile_range(b, p, lo, hi, grid, a, s));
+  }
+  return DG_OK;
+}
+
 void drop_graphs(dg_batch* b) {
   for (auto& row : b->graph)
     for (auto& g : row)
@@ -250,12 +290,16 @@ dg_status get_graph(dg_batch* b, cudaGraphExec_t* out) {
 // tile_tx x tile_ty quads, in the same order of orders.
 dg_status build_items_impl(dg_batch* b, int block, const int* shapes) {
   std::vector<BatchItem> items;
+  std::vector<int> lo, hi;
   int begin[4] = {0, 0, 0, 0}, end[4] = {0, 0, 0, 0};
   try {
+    lo.assign(b->n, 0);
+    hi.assign(b->n, 0);
     for (int p = 3; p >= 1; --p) {
       begin[p] = (int)std::min(items.size(), (size_t)INT_MAX);
       for (int i = 0; i < b->n; ++i) {
         if (b->inst[i].p != p) continue;
+        lo[i] = (int)std::min(items.size(), (size_t)INT_MAX);
         if (b->tiled) {
           const int tx = tile_tx(shapes[p]), ty = tile_ty(shapes[p]);
           const long long nt = (long long)((b->inst[i].cfg.nx + tx - 1) / tx) * ((b->inst[i].cfg.ny + ty - 1) / ty);
@@ -263,6 +307,7 @@ dg_status build_items_impl(dg_batch* b, int block, const int* shapes) {
         } else {
           for (long long s = 0; s < b->inst[i].E; s += block) items.push_back({i, (int)s});
         }
+        hi[i] = (int)std::min(items.size(), (size_t)INT_MAX);
       }
       end[p] = (int)std::min(items.size(), (size_t)INT_MAX);
     }
@@ -313,6 +358,8 @@ dg_status build_items_impl(dg_batch* b, int block, const int* shapes) {
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = d_new;
   b->n_items = (int)items.size();
+  b->item_lo.swap(lo);
+  b->item_hi.swap(hi);
   b->block = block;
   b->grid = grid;
   for (int p = 0; p < 4; ++p) {
@@ -339,6 +386,13 @@ void free_batch(dg_batch* b) {
   for (void* p : bufs)
     if (p) cudaFree(p);
   if (b->cap) cudaStreamDestroy(b->cap);
+  for (cudaStream_t s : {b->s_up, b->s_down})
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->ev_up) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->ev_done) cudaEventDestroy(e);
+  for (cudaEvent_t e : {b->ev_start, b->ev_end})
+    if (e) cudaEventDestroy(e);
+  if (b->pcount) cudaFree(b->pcount);
   delete b;
 }
 
@@ -725,6 +779,196 @@ dg_status dg_batch_get_states(dg_batch* b, double* const* xi, double* const* qx,
   }
   CK(cudaStreamSynchronize(b->stream));
   return DG_OK;
+}
+
+// Groups of dg_batch_step_host: tile-fused batches split every order class
+// (p = 3 first) into runs of consecutive instances of about 1/16 of the
+// batch's state bytes each (one instance at least), so that copies and
+// compute overlap finely; other batches form one group.
+constexpr int kStepGroups = 16;
+struct StepGroup {
+  int p, lo, hi;              // order class, items [lo, hi)
+  std::vector<int> inst;      // its instances
+};
+
+static dg_status make_groups(const dg_batch* b, std::vector<StepGroup>& gs) {
+  try {
+    gs.clear();
+    if (!b->tiled) {
+      StepGroup g{0, 0, 0, {}};
+      for (int i = 0; i < b->n; ++i) g.inst.push_back(i);
+      gs.push_back(std::move(g));
+      return DG_OK;
+    }
+    double total = 0.0;
+    for (const HostInst& h : b->inst) total += 24.0 * h.K * h.E;
+    const double target = total / kStepGroups;
+    for (int p = 3; p >= 1; --p) {
+      StepGroup g{p, 0, 0, {}};
+      double bytes = 0.0;
+      for (int i = 0; i < b->n; ++i) {
+        if (b->inst[i].p != p) continue;
+        if (g.inst.empty()) g.lo = b->item_lo[i];
+        g.inst.push_back(i);
+        g.hi = b->item_hi[i];
+        bytes += 24.0 * b->inst[i].K * b->inst[i].E;
+        if (bytes >= target) {
+          gs.push_back(std::move(g));
+          g = StepGroup{p, 0, 0, {}};
+          bytes = 0.0;
+        }
+      }
+      if (!g.inst.empty()) gs.push_back(std::move(g));
+    }
+  } catch (const std::exception&) {
+    return DG_ERR_OOM;
+  }
+  return DG_OK;
+}
+
+// Copy streams, events and work counters of dg_batch_step_host
+// (non-blocking streams: no implicit ordering with a legacy default
+// stream; all ordering is by events)
+static dg_status ensure_pipeline(dg_batch* b, size_t groups) {
+  if (!b->s_up) CK(cudaStreamCreateWithFlags(&b->s_up, cudaStreamNonBlocking));
+  if (!b->s_down) CK(cudaStreamCreateWithFlags(&b->s_down, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&b->ev_start, &b->ev_end})
+    if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  try {
+    while (b->ev_up.size() < groups) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      CK(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+      const cudaError_t ce = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+      if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return cuda_status(ce);
+      }
+      b->ev_up.push_back(e0);
+      b->ev_done.push_back(e1);
+    }
+  } catch (const std::exception&) {
+    return DG_ERR_OOM;
+  }
+  // sized once for the largest group count make_groups can give (at most
+  // kStepGroups + 3: every class ends one partial group)
+  if (!b->pcount) CK(cudaMalloc((void**)&b->pcount, sizeof(unsigned) * b->S * (kStepGroups + 3)));
+  return DG_OK;
+}
+
+static dg_status step_host_impl(dg_batch* b, const double* const* xi_in, const double* const* qx_in,
+                                const double* const* qy_in, double* const* xi_out, double* const* qx_out,
+                                double* const* qy_out, double* t_out) {
+  std::vector<StepGroup> gs;
+  dg_status s = make_groups(b, gs);
+  if (s == DG_OK) s = ensure_batch_stage(b, b->stage_total);
+  if (s == DG_OK) s = ensure_pipeline(b, gs.size());
+  if (s != DG_OK) return s;
+  const int ng = (int)gs.size();
+  const cudaStream_t c = b->stream, up = b->s_up, down = b->s_down;
+  // the copies start after the work already queued on the batch's stream
+  CK(cudaEventRecord(b->ev_start, c));
+  CK(cudaStreamWaitEvent(up, b->ev_start, 0));
+  CK(cudaStreamWaitEvent(down, b->ev_start, 0));
+  const double* const* in[3] = {xi_in, qx_in, qy_in};
+  double* const* out[3] = {xi_out, qx_out, qy_out};
+  // uploads, group by group (copy engine)
+  for (int g = 0; g < ng; ++g) {
+    for (int i : gs[g].inst) {
+      const HostInst& h = b->inst[i];
+      const long long KE = (long long)h.K * h.E;
+      for (int f = 0; f < 3; ++f)
+        CK(cudaMemcpyAsync(b->stage + h.o_stage + (size_t)f * KE, in[f][i], sizeof(double) * KE,
+                           cudaMemcpyHostToDevice, up));
+    }
+    CK(cudaEventRecord(b->ev_up[g], up));
+  }
+  // compute: every group's state in, evaluated, stepped and out to staging
+  // as soon as its upload is done; later groups' uploads and earlier
+  // groups' downloads overlap it
+  const int ep = b->ep, lc = b->lc;
+  if (b->tiled) {
+    CK(cudaMemsetAsync(b->pcount, 0, sizeof(unsigned) * b->S * ng, c));
+    CK(cudaMemsetAsync(b->lam + (size_t)lc * b->n, 0, sizeof(double) * b->n, c));
+    if (b->adaptive) CK(cudaMemsetAsync(b->lam + (size_t)(1 - lc) * b->n, 0, sizeof(double) * b->n, c));
+  }
+  for (int g = 0; g < ng; ++g) {
+    CK(cudaStreamWaitEvent(c, b->ev_up[g], 0));
+    for (int i : gs[g].inst) {
+      const HostInst& h = b->inst[i];
+      const unsigned gr = (unsigned)((h.E + 127) / 128);
+      char* dst = (char*)b->w[0] + h.o_state;
+      if (b->arith == ARITH_FP64)
+        aos_to_soa_kernel<double><<<gr, 128, 0, c>>>(b->stage + h.o_stage, (double*)dst, h.E, h.K, 3);
+      else
+        aos_to_soa_kernel<float><<<gr, 128, 0, c>>>(b->stage + h.o_stage, (float*)dst, h.E, h.K, 3);
+      CK(cudaGetLastError());
+      if (b->tiled) CK(launch_wave_speed(b, i, c));
+    }
+    if (b->tiled) {
+      s = launch_range_step(b, gs[g].p, gs[g].lo, gs[g].hi, b->pcount + (size_t)g * b->S, ep, lc, c);
+    } else {
+      b->evaluated = false;
+      s = launch_eval(b, c);
+      cudaGraphExec_t gx;
+      if (s == DG_OK) s = get_graph(b, &gx);
+      if (s == DG_OK) CK(cudaGraphLaunch(gx, c));
+    }
+    if (s != DG_OK) return s;
+    for (int i : gs[g].inst) {
+      const HostInst& h = b->inst[i];
+      const unsigned gr = (unsigned)((h.E + 127) / 128);
+      const char* src = (const char*)b->w[0] + h.o_state;
+      if (b->arith == ARITH_FP64)
+        soa_to_aos_kernel<double><<<gr, 128, 0, c>>>((const double*)src, b->stage + h.o_stage, h.E, h.K, 3);
+      else
+        soa_to_aos_kernel<float><<<gr, 128, 0, c>>>((const float*)src, b->stage + h.o_stage, h.E, h.K, 3);
+      CK(cudaGetLastError());
+    }
+    CK(cudaEventRecord(b->ev_done[g], c));
+    // downloads of this group (copy engine)
+    CK(cudaStreamWaitEvent(down, b->ev_done[g], 0));
+    for (int i : gs[g].inst) {
+      const HostInst& h = b->inst[i];
+      const long long KE = (long long)h.K * h.E;
+      for (int f = 0; f < 3; ++f)
+        CK(cudaMemcpyAsync(out[f][i], b->stage + h.o_stage + (size_t)f * KE, sizeof(double) * KE,
+                           cudaMemcpyDeviceToHost, down));
+    }
+  }
+  CK(cudaEventRecord(b->ev_end, down));
+  CK(cudaStreamWaitEvent(c, b->ev_end, 0));
+  b->ep = (b->ep + b->S) & 1;
+  if (b->adaptive) b->lc = 1 - b->lc;
+  b->evaluated = true;
+  unsigned herr = 0;
+  CK(cudaMemcpyAsync(&herr, b->err, sizeof herr, cudaMemcpyDeviceToHost, c));
+  if (t_out) CK(cudaMemcpyAsync(t_out, b->t, sizeof(double) * b->n, cudaMemcpyDeviceToHost, c));
+  CK(cudaStreamSynchronize(c));
+  if (herr) {
+    CK(cudaMemsetAsync(b->err, 0, sizeof(unsigned), c));
+    CK(cudaStreamSynchronize(c));
+  }
+  if (herr & ERRF_NONFINITE) return DG_ERR_NONFINITE;
+  if (herr & ERRF_DRY) return DG_ERR_DRY;
+  return DG_OK;
+}
+
+dg_status dg_batch_step_host(dg_batch* b, const double* const* xi_in, const double* const* qx_in,
+                             const double* const* qy_in, double* const* xi_out, double* const* qx_out,
+                             double* const* qy_out, double* t_out) {
+  dgswe::NvtxRange nvtx_range("dg_batch_step_host");
+  if (!b || !xi_in || !qx_in || !qy_in || !xi_out || !qx_out || !qy_out) return DG_ERR_ARG;
+  for (int i = 0; i < b->n; ++i)
+    if (!xi_in[i] || !qx_in[i] || !qy_in[i] || !xi_out[i] || !qx_out[i] || !qy_out[i]) return DG_ERR_ARG;
+  const dg_status s = step_host_impl(b, xi_in, qx_in, qy_in, xi_out, qx_out, qy_out, t_out);
+  if (s != DG_OK && s != DG_ERR_DRY && s != DG_ERR_NONFINITE) {
+    // a launch failed part-way: let the copies already queued finish before
+    // the caller's arrays may go away
+    if (b->s_up) cudaStreamSynchronize(b->s_up);
+    if (b->s_down) cudaStreamSynchronize(b->s_down);
+    cudaStreamSynchronize(b->stream);
+  }
+  return s;
 }
 
 dg_status dg_batch_set_state(dg_batch* b, int i, const double* xi, const double* qx, const double* qy, double t) {

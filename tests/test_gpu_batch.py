@@ -131,6 +131,50 @@ def test_batch_state_through_page_locked_host_arrays():
             B.dg_batch_destroy(b2)
 
 
+@pytest.mark.parametrize("precision,proj", [("fp32", "mixed"), ("fp32", "fp64"), ("fp64", "fp64")])
+def test_batch_step_host_matches_set_run_get(precision, proj):
+    """dg_batch_step_host (pipelined per order class in the tile-fused FP32
+    batch, one group in the per-element ones) gives the bits of
+    dg_batch_set_state for every instance + dg_batch_run(b, 1) +
+    dg_batch_get_states, over three consecutive steps: page-locked inputs
+    with pageable outputs, pageable inputs with the output aliasing them,
+    page-locked inputs and outputs"""
+    inst = [_instance(k, *s, precision, proj) for k, s in enumerate(SPECS)]
+    args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
+            [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
+    shapes = [(E, K) for _, _, E, K in inst]
+    b1 = B.dg_batch_init_device(*args)
+    b2 = B.dg_batch_init_device(*args)
+
+    def pinned_copy(states):
+        return [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in st] for st in states]
+    try:
+        B.dg_batch_run(b1, 2)
+        B.dg_batch_run(b2, 2)
+        ref = B.dg_batch_get_states(b1, shapes)
+        cur2 = pinned_copy(ref)
+        for step in range(3):
+            tnow = B.dg_batch_run(b1, 0)
+            for i in range(len(inst)):
+                B.dg_batch_set_state(b1, i, *ref[i], t=float(tnow[i]))
+            t1 = B.dg_batch_run(b1, 1)
+            ref = B.dg_batch_get_states(b1, shapes)
+            if step == 0:
+                got, t2 = B.dg_batch_step_host(b2, shapes, cur2)
+            elif step == 1:
+                got, t2 = B.dg_batch_step_host(b2, shapes, cur2, out=cur2)
+            else:
+                got, t2 = B.dg_batch_step_host(b2, shapes, pinned_copy(cur2), out=pinned_copy(cur2))
+            assert np.array_equal(t1, t2), (step, t1, t2)
+            for i in range(len(inst)):
+                for a, r in zip(got[i], ref[i]):
+                    assert np.array_equal(a, r), (precision, proj, step, i)
+            cur2 = [[np.array(a) for a in st] for st in got]
+    finally:
+        B.dg_batch_destroy(b1)
+        B.dg_batch_destroy(b2)
+
+
 @pytest.mark.parametrize("tile", [1, -1])
 def test_batch_autotune_keeps_state(tile):
     """the autotuner (tile shapes of a tile-fused batch, elements per work

@@ -197,6 +197,7 @@ def test_null_handles_are_rejected(lib):
     assert L.dg_batch_set_block(None, 64) == B.DG_ERR_ARG
     assert L.dg_batch_get_state(None, 0, None, None, None) == B.DG_ERR_ARG
     assert L.dg_batch_get_states(None, None, None, None) == B.DG_ERR_ARG
+    assert L.dg_batch_step_host(None, None, None, None, None, None, None, None) == B.DG_ERR_ARG
     assert L.dg_batch_set_state(None, 0, None, None, None, 0.0) == B.DG_ERR_ARG
     assert L.dg_batch_autotune(None, 1, None, None) == B.DG_ERR_ARG
     assert L.dg_batch_dofs(None) == 0
