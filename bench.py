@@ -309,10 +309,9 @@ def run_batch(args, wls):
         # state comes back to the host (dg_batch_step_host: the three
         # pipelined over groups of instances); one untimed call first, which
         # allocates the staging area
-        host = [[torch.empty((wl.E, wl.K), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
-                for wl in wls]
         shapes = [(wl.E, wl.K) for wl in wls]
-        B.dg_batch_get_states(b, shapes, out=host)
+        host = B.HostStates(shapes, pinned=True)
+        B.dg_batch_get_states(b, shapes, out=host.arrays)
         B.dg_batch_step_host(b, shapes, host, out=host)
         n_e2e = max(1, min(args.steps, args.e2e_steps))
         torch.cuda.synchronize()

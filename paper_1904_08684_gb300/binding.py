@@ -112,7 +112,7 @@ def load(build_if_missing=True):
     lib.dg_batch_run.argtypes = [vp, ctypes.c_int, dp]
     lib.dg_batch_get_state.argtypes = [vp, ctypes.c_int, dp, dp, dp]
     lib.dg_batch_get_states.argtypes = [vp, dpp, dpp, dpp]
-    lib.dg_batch_step_host.argtypes = [vp, dpp, dpp, dpp, dpp, dpp, dpp, dp]
+    lib.dg_batch_step_host.argtypes = [vp, vpp, vpp, vpp, vpp, vpp, vpp, dp]
     lib.dg_batch_set_state.argtypes = [vp, ctypes.c_int, dp, dp, dp, ctypes.c_double]
     lib.dg_batch_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), dp]
     lib.dg_batch_set_block.argtypes = [vp, ctypes.c_int]
@@ -344,29 +344,47 @@ def dg_batch_get_states(b, shapes, out=None):
     return out
 
 
+class HostStates:
+    """Host states of every instance of a batch, [[xi, qx, qy] per
+    instance] as (E_i, K_i) FP64 arrays, with the C pointer arrays of
+    dg_batch_step_host built once (the arrays must stay alive and in place;
+    reuse the object across steps to skip the marshalling)."""
+
+    def __init__(self, shapes, arrays=None, pinned=False):
+        if arrays is None:
+            if pinned:
+                import torch
+                arrays = [[torch.zeros((E, K), dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
+                          for E, K in shapes]
+            else:
+                arrays = [[np.zeros((E, K)) for _ in range(3)] for E, K in shapes]
+        if len(arrays) != len(shapes):
+            raise ValueError("expected %d instances, got %d" % (len(shapes), len(arrays)))
+        n = len(shapes)
+        cols = [[0] * n for _ in range(3)]
+        for i, ((E, K), st) in enumerate(zip(shapes, arrays)):
+            for f, a in enumerate(st):
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.size != E * K:
+                    raise ValueError("instance %d: expected contiguous float64 of %d x %d" % (i, E, K))
+                cols[f][i] = a.ctypes.data
+        self.arrays = arrays
+        self.ptrs = [(ctypes.c_void_p * n)(*c) for c in cols]
+
+
 def dg_batch_step_host(b, shapes, states, out=None):
-    """one step of every instance from host states to host states:
-    states = [[xi, qx, qy] per instance] (host (E_i, K_i) FP64 arrays);
-    returns (out, t) with out in the same form (``states`` itself may be
-    passed as ``out``) and t the instances' times after the step"""
-    n = len(shapes)
+    """one step of every instance from host states to host states: states
+    and out are HostStates or lists [[xi, qx, qy] per instance] of host
+    (E_i, K_i) FP64 arrays (out may be the same object as states; None:
+    new pageable arrays).  Returns (out arrays, t after the step)."""
+    if not isinstance(states, HostStates):
+        states = HostStates(shapes, [[np.ascontiguousarray(a, dtype=np.float64) for a in st] for st in states])
     if out is None:
-        out = [[np.zeros((E, K)) for _ in range(3)] for E, K in shapes]
-    if len(states) != n or len(out) != n:
-        raise ValueError("expected %d instances" % n)
-    ptrs = [(ctypes.POINTER(ctypes.c_double) * n)() for _ in range(6)]
-    keep = []
-    for i, (E, K) in enumerate(shapes):
-        for f in range(3):
-            a = _host(states[i][f], E, K)
-            keep.append(a)
-            ptrs[f][i] = _hptr(a)
-            o = out[i][f]
-            assert o.dtype == np.float64 and o.flags.c_contiguous and o.size == E * K
-            ptrs[3 + f][i] = _hptr(o)
-    t = np.zeros(n)
-    _check(load().dg_batch_step_host(b, *ptrs, _hptr(t)), "dg_batch_step_host")
-    return out, t
+        out = HostStates(shapes)
+    elif not isinstance(out, HostStates):
+        out = HostStates(shapes, out)
+    t = np.zeros(len(shapes))
+    _check(load().dg_batch_step_host(b, *states.ptrs, *out.ptrs, _hptr(t)), "dg_batch_step_host")
+    return out.arrays, t
 
 
 def dg_batch_set_state(b, i, xi, qx, qy, t=0.0):

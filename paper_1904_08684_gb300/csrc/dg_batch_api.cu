@@ -51,6 +51,78 @@ struct HostInst {
   size_t o_stage;                                            // offset (doubles) of its staging slice
 };
 
+// Instance record of dg_batch_step_host's per-group kernels (one row of
+// blocks per instance: blockIdx.y)
+struct XferInst {
+  double* stage;     // its staging slice [3][E][K], FP64 element-major
+  void* state;       // its state [3][K][E] in the batch's precision
+  const void* hb;    // its h_b coefficients (the first E are the element means)
+  long long E;
+  int K, i;          // coefficients per field; instance index
+  float g;
+};
+
+// staging slices <-> states of a group's instances: a transpose through
+// shared memory, 256 elements of one field at a time, coalesced on both
+// sides (the slice's [E][K] run of those elements, the state's K rows);
+// one padding word per 32 breaks the bank conflicts of the K-strided
+// accesses
+constexpr int kXferTile = 256;
+constexpr int kXferWords = kXferTile * 15;   // K <= 15
+__device__ __forceinline__ int xfer_pad(int j) { return j + (j >> 5); }
+
+template <class Real>
+__global__ void __launch_bounds__(kXferTile) group_in_kernel(const XferInst* __restrict__ t, int first) {
+  __shared__ double tile[kXferWords + kXferWords / 32];
+  const XferInst x = t[first + blockIdx.y];
+  const int K = x.K, tid = threadIdx.x;
+  Real* w = static_cast<Real*>(x.state);
+  for (long long e0 = (long long)blockIdx.x * kXferTile; e0 < x.E; e0 += (long long)gridDim.x * kXferTile) {
+    const int ne = (int)(x.E - e0 < kXferTile ? x.E - e0 : kXferTile);
+    for (int f = 0; f < 3; ++f) {
+      const double* src = x.stage + ((long long)f * x.E + e0) * K;
+      for (int j = tid; j < ne * K; j += kXferTile) tile[xfer_pad(j)] = src[j];
+      __syncthreads();
+      if (tid < ne)
+        for (int k = 0; k < K; ++k) w[((long long)f * K + k) * x.E + e0 + tid] = Real(tile[xfer_pad(tid * K + k)]);
+      __syncthreads();
+    }
+  }
+}
+template <class Real>
+__global__ void __launch_bounds__(kXferTile) group_out_kernel(const XferInst* __restrict__ t, int first) {
+  __shared__ double tile[kXferWords + kXferWords / 32];
+  const XferInst x = t[first + blockIdx.y];
+  const int K = x.K, tid = threadIdx.x;
+  const Real* w = static_cast<const Real*>(x.state);
+  for (long long e0 = (long long)blockIdx.x * kXferTile; e0 < x.E; e0 += (long long)gridDim.x * kXferTile) {
+    const int ne = (int)(x.E - e0 < kXferTile ? x.E - e0 : kXferTile);
+    for (int f = 0; f < 3; ++f) {
+      if (tid < ne)
+        for (int k = 0; k < K; ++k) tile[xfer_pad(tid * K + k)] = double(w[((long long)f * K + k) * x.E + e0 + tid]);
+      __syncthreads();
+      double* dst = x.stage + ((long long)f * x.E + e0) * K;
+      for (int j = tid; j < ne * K; j += kXferTile) dst[j] = tile[xfer_pad(j)];
+      __syncthreads();
+    }
+  }
+}
+// CFL maxima of a group's FP32 states into lam_row[i] (zeroed by the caller),
+// with the operations of wave_speed_kernel<float>
+__global__ void __launch_bounds__(256) group_wave_speed_kernel(const XferInst* __restrict__ t, int first,
+                                                               double* lam_row) {
+  const XferInst x = t[first + blockIdx.y];
+  const float* w = static_cast<const float*>(x.state);
+  const float* hb = static_cast<const float*>(x.hb);
+  double l = 0.0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < x.E; e += (long long)gridDim.x * blockDim.x) {
+    const float H0 = w[e] + hb[e];
+    l = fmax(l, double(element_wave_speed_H(H0, w[(long long)x.K * x.E + e], w[2LL * x.K * x.E + e], x.g)));
+  }
+  l = block_max(l);
+  if (threadIdx.x == 0) atomic_max_nonneg(lam_row + x.i, l);
+}
+
 }  // namespace
 
 struct dg_batch {
@@ -96,6 +168,7 @@ struct dg_batch {
   std::vector<cudaEvent_t> ev_up, ev_done;
   cudaEvent_t ev_start = nullptr, ev_end = nullptr;
   unsigned* pcount = nullptr;         // [groups][S]
+  XferInst* xfer = nullptr;           // [n] per-instance records, in group order
   long long dofs = 0;
 };
 
@@ -393,6 +466,7 @@ void free_batch(dg_batch* b) {
   for (cudaEvent_t e : {b->ev_start, b->ev_end})
     if (e) cudaEventDestroy(e);
   if (b->pcount) cudaFree(b->pcount);
+  if (b->xfer) cudaFree(b->xfer);
   delete b;
 }
 
@@ -864,6 +938,31 @@ static dg_status step_host_impl(dg_batch* b, const double* const* xi_in, const d
   if (s == DG_OK) s = ensure_pipeline(b, gs.size());
   if (s != DG_OK) return s;
   const int ng = (int)gs.size();
+  // per-instance records in group order (the groups depend only on the
+  // instances' sizes: built once)
+  std::vector<int> first(ng + 1, 0);
+  for (int g = 0; g < ng; ++g) first[g + 1] = first[g] + (int)gs[g].inst.size();
+  if (!b->xfer) {
+    std::vector<XferInst> tab;
+    try {
+      for (const StepGroup& g : gs)
+        for (int i : g.inst) {
+          const HostInst& h = b->inst[i];
+          tab.push_back({b->stage + h.o_stage, (char*)b->w[0] + h.o_state, (const char*)b->hb + h.o_hb, h.E, h.K, i,
+                         float(h.cfg.g)});
+        }
+    } catch (const std::exception&) {
+      return DG_ERR_OOM;
+    }
+    XferInst* d = nullptr;
+    CK(cudaMalloc((void**)&d, sizeof(XferInst) * tab.size()));
+    const cudaError_t ce = cudaMemcpy(d, tab.data(), sizeof(XferInst) * tab.size(), cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+      cudaFree(d);
+      return cuda_status(ce);
+    }
+    b->xfer = d;
+  }
   const cudaStream_t c = b->stream, up = b->s_up, down = b->s_down;
   // the copies start after the work already queued on the batch's stream
   CK(cudaEventRecord(b->ev_start, c));
@@ -893,16 +992,18 @@ static dg_status step_host_impl(dg_batch* b, const double* const* xi_in, const d
   }
   for (int g = 0; g < ng; ++g) {
     CK(cudaStreamWaitEvent(c, b->ev_up[g], 0));
-    for (int i : gs[g].inst) {
-      const HostInst& h = b->inst[i];
-      const unsigned gr = (unsigned)((h.E + 127) / 128);
-      char* dst = (char*)b->w[0] + h.o_state;
-      if (b->arith == ARITH_FP64)
-        aos_to_soa_kernel<double><<<gr, 128, 0, c>>>(b->stage + h.o_stage, (double*)dst, h.E, h.K, 3);
-      else
-        aos_to_soa_kernel<float><<<gr, 128, 0, c>>>(b->stage + h.o_stage, (float*)dst, h.E, h.K, 3);
+    // the group's staging slices -> states, then (tile-fused) their CFL
+    // maxima: one launch each, one row of blocks per instance
+    const int ni = first[g + 1] - first[g];
+    const dim3 grid((unsigned)std::max(16, 1216 / ni), (unsigned)ni);
+    if (b->arith == ARITH_FP64)
+      group_in_kernel<double><<<grid, 256, 0, c>>>(b->xfer, first[g]);
+    else
+      group_in_kernel<float><<<grid, 256, 0, c>>>(b->xfer, first[g]);
+    CK(cudaGetLastError());
+    if (b->tiled) {
+      group_wave_speed_kernel<<<grid, 256, 0, c>>>(b->xfer, first[g], b->lam + (size_t)lc * b->n);
       CK(cudaGetLastError());
-      if (b->tiled) CK(launch_wave_speed(b, i, c));
     }
     if (b->tiled) {
       s = launch_range_step(b, gs[g].p, gs[g].lo, gs[g].hi, b->pcount + (size_t)g * b->S, ep, lc, c);
@@ -914,16 +1015,11 @@ static dg_status step_host_impl(dg_batch* b, const double* const* xi_in, const d
       if (s == DG_OK) CK(cudaGraphLaunch(gx, c));
     }
     if (s != DG_OK) return s;
-    for (int i : gs[g].inst) {
-      const HostInst& h = b->inst[i];
-      const unsigned gr = (unsigned)((h.E + 127) / 128);
-      const char* src = (const char*)b->w[0] + h.o_state;
-      if (b->arith == ARITH_FP64)
-        soa_to_aos_kernel<double><<<gr, 128, 0, c>>>((const double*)src, b->stage + h.o_stage, h.E, h.K, 3);
-      else
-        soa_to_aos_kernel<float><<<gr, 128, 0, c>>>((const float*)src, b->stage + h.o_stage, h.E, h.K, 3);
-      CK(cudaGetLastError());
-    }
+    if (b->arith == ARITH_FP64)
+      group_out_kernel<double><<<grid, 256, 0, c>>>(b->xfer, first[g]);
+    else
+      group_out_kernel<float><<<grid, 256, 0, c>>>(b->xfer, first[g]);
+    CK(cudaGetLastError());
     CK(cudaEventRecord(b->ev_done[g], c));
     // downloads of this group (copy engine)
     CK(cudaStreamWaitEvent(down, b->ev_done[g], 0));

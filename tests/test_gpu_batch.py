@@ -138,7 +138,7 @@ def test_batch_step_host_matches_set_run_get(precision, proj):
     dg_batch_set_state for every instance + dg_batch_run(b, 1) +
     dg_batch_get_states, over three consecutive steps: page-locked inputs
     with pageable outputs, pageable inputs with the output aliasing them,
-    page-locked inputs and outputs"""
+    page-locked inputs and outputs (prebuilt HostStates)"""
     inst = [_instance(k, *s, precision, proj) for k, s in enumerate(SPECS)]
     args = ([c for c, *_ in inst], [f[0] for _, f, _, _ in inst], [f[1] for _, f, _, _ in inst],
             [f[2] for _, f, _, _ in inst], [f[3] for _, f, _, _ in inst])
@@ -164,7 +164,8 @@ def test_batch_step_host_matches_set_run_get(precision, proj):
             elif step == 1:
                 got, t2 = B.dg_batch_step_host(b2, shapes, cur2, out=cur2)
             else:
-                got, t2 = B.dg_batch_step_host(b2, shapes, pinned_copy(cur2), out=pinned_copy(cur2))
+                got, t2 = B.dg_batch_step_host(b2, shapes, B.HostStates(shapes, pinned_copy(cur2)),
+                                               out=B.HostStates(shapes, pinned=True))
             assert np.array_equal(t1, t2), (step, t1, t2)
             for i in range(len(inst)):
                 for a, r in zip(got[i], ref[i]):
