@@ -337,7 +337,8 @@ dg_status dg_batch_get_state(dg_batch* b, int i, double* xi, double* qx, double*
  * on an error some instances may have been written. */
 dg_status dg_batch_get_states(dg_batch* b, double* const* xi, double* const* qx, double* const* qy);
 
-/* One SSP-RK step (reading R6) of every instance from host states to host
+/* One SSP-RK step (as dg_rk_step: the scheme of paper §2.2 with this
+ * library's SSP Runge-Kutta time step) of every instance from host states to host
  * states, as dg_batch_set_state(b, i, xi_in[i], qx_in[i], qy_in[i], t_i)
  * for every i (t_i its current time), dg_batch_run(b, 1, t_out) and
  * dg_batch_get_states(b, xi_out, qx_out, qy_out) would do, with the same
