@@ -350,9 +350,13 @@ def run_batch(args, wls):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         picks = [next(wl for wl in wls if wl.p == q) for q in (1, 2, 3) if any(w.p == q for w in wls)]
         parts = [cpu_baseline(wl, args.cpu_seconds / len(picks)) for wl in picks]
-        out["cpu_baseline"] = {"value": sum(pp["value"] for pp in parts) / len(parts), "unit": UNIT,
-                               "cores": parts[0]["cores"], "kind": "oracle",
-                               "sample": "; ".join(pp["sample"] for pp in parts) + " (mean of the p classes)"}
+        # the whole ensemble at each order class's sampled rate, weighted by
+        # the class's share of the ensemble's DOFs
+        share = [sum(w.dofs() for w in wls if w.p == wl.p) for wl in picks]
+        value = sum(share) / sum(sh / pp["value"] for sh, pp in zip(share, parts))
+        out["cpu_baseline"] = {"value": value, "unit": UNIT, "cores": parts[0]["cores"], "kind": "oracle",
+                               "sample": "; ".join(pp["sample"] for pp in parts)
+                               + " (every order class weighted by its share of the ensemble's DOFs)"}
     return out
 
 
@@ -486,37 +490,52 @@ def run_reference(args):
     world, rank, local = _dist()
     if rank != 0:
         return
-    wls = WORKLOADS[args.workload]()
-    if isinstance(wls, list):                     # ensemble: one instance per order
-        wls = [next(w for w in wls if w.p == q) for q in (1, 2, 3) if any(w.p == q for w in wls)]
+    all_wls = WORKLOADS[args.workload]()
+    ens = isinstance(all_wls, list)
+    if ens:                                       # ensemble: one instance per order
+        wls = [next(w for w in all_wls if w.p == q) for q in (1, 2, 3) if any(w.p == q for w in all_wls)]
     else:
-        wls = [wls]
+        wls = [all_wls]
     samples = [_oracle_sample(w) for w in wls]
     per_step = max(0.5, args.cpu_seconds / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         for sm in samples:
             _time_sample(sm, per_step / len(samples))
-    dofs = el = 0.0
+    d_s = [0.0] * len(samples)
+    e_s = [0.0] * len(samples)
     reps = 0
     for _ in range(args.steps):
-        for sm in samples:
+        for k, sm in enumerate(samples):
             d, e, r = _time_sample(sm, per_step / len(samples))
-            dofs += d
-            el += e
+            d_s[k] += d
+            e_s[k] += e
             reps += r
-    value = dofs / el
-    wl = wls[0]
-    sample = "oracle RHS (one RK stage) of 1/16 of the elements of %s, %d evaluations in %.1f s" % (
-        ", ".join(w.name for w in wls), reps, el)
+    el = sum(e_s)
+    if ens:
+        # the whole ensemble's throughput: every order class's DOFs at the
+        # rate measured on its sampled instance
+        share = [sum(w.dofs() for w in all_wls if w.p == wl.p) for wl in wls]
+        value = sum(share) / sum(sh * e / d for sh, d, e in zip(share, d_s, e_s))
+        config = {"workload": args.workload, "instances": len(all_wls),
+                  "p_counts": {str(q): sum(1 for w in all_wls if w.p == q) for q in (1, 2, 3)},
+                  "dof_per_stage": sum(w.dofs() for w in all_wls), "rk_stages": wls[0].rk_order,
+                  "precision": "fp64", "parallelism": "host cores"}
+        how = "; every order class weighted by its share of the ensemble's DOFs"
+    else:
+        value = sum(d_s) / el
+        wl = wls[0]
+        config = {"workload": args.workload, "elements": wl.E, "p": wl.p, "K": wl.K,
+                  "rk_stages": wl.rk_order, "precision": "fp64", "bc": wl.bc}
+        how = ""
+    sample = "oracle RHS (one RK stage) of 1/16 of the elements of %s, %d evaluations in %.1f s%s" % (
+        ", ".join(w.name for w in wls), reps, el, how)
     # n_gpus: the launch's N (the oracle itself runs on rank 0's host cores)
-    ens = args.workload.startswith("ensemble")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "device": "host CPU cores (FP64 oracle)",
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
            "higher_is_better": True, "scaling": "strong" if ens else "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded SplitMix64 fields)",
-           "config": {"workload": args.workload, "elements": wl.E, "p": wl.p, "K": wl.K,
-                      "rk_stages": wl.rk_order, "precision": "fp64", "bc": wl.bc},
+           "config": config,
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": samples[0][0].threads(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
