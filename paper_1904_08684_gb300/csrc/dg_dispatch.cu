@@ -123,7 +123,8 @@ DGSWE_AUX_DISPATCH(fp32p32)
 DGSWE_AUX_DISPATCH(fp32pdf)
 DGSWE_AUX_DISPATCH(fp32pir)
 
-// static bathymetry matrix of the mixed solve (FP64 sums stored as float pairs)
+// static bathymetry matrix of the mixed solve (the low parts of its FP64 sums; at
+// p = 4 also the FP32 parts, see ahb_keeps_hi)
 cudaError_t static_ahb(int p, const Mesh& m, const double* hb64, float* ahb, cudaStream_t s) {
   const unsigned g = (unsigned)((m.E + 127) / 128);
   switch (p) {

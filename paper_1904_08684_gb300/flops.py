@@ -52,12 +52,43 @@ KERNEL_SOURCES = ("dg_aux_inst.cu", "dg_batch.cuh", "dg_batch_inst.cu", "dg_disp
                   "dg_launch.cuh", "dg_stage_inst.cu", "dg_tile.cuh", "dg_tile_inst.cu", "dg_batch_tile_inst.cu", "gen_tables.py")
 
 
-def source_hash():
-    """hash of the kernel sources: measured traffic is valid only for it"""
+def _code_only(name, text):
+    """C/C++ source without its comments and blank-line or trailing-space
+    differences (a comment edit changes no kernel); other files verbatim"""
+    if not name.endswith((".cu", ".cuh", ".h")):
+        return text
+    out, i, n = [], 0, len(text)
+    while i < n:
+        if text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+        elif text[i] == '"':                       # string literal, kept whole
+            j = i + 1
+            while j < n and text[j] != '"':
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        else:
+            out.append(text[i])
+            i += 1
+    lines = [ln.rstrip() for ln in "".join(out).split("\n")]
+    return "\n".join(ln for ln in lines if ln)
+
+
+def source_hash(read=None):
+    """hash of the kernel sources' code (comments ignored): measured traffic
+    is valid only for it.  read(name) -> text overrides reading csrc/."""
     h = hashlib.sha1()
     for name in KERNEL_SOURCES:
-        with open(os.path.join(_CSRC, name), "rb") as f:
-            h.update(name.encode() + f.read())
+        if read is None:
+            with open(os.path.join(_CSRC, name), encoding="utf-8") as f:
+                text = f.read()
+        else:
+            text = read(name)
+        h.update((name + _code_only(name, text)).encode())
     return h.hexdigest()[:16]
 
 

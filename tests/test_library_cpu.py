@@ -223,3 +223,21 @@ def test_tile_shape_is_validated(lib):
     for bad in (-2, 4):
         cfg = B.make_config(4, 4, 1, precision="fp32", tile_shape=bad)
         assert B.load().dg_init(ctypes.byref(cfg), z, z, z, z, None, ctypes.byref(h)) == B.DG_ERR_ARG
+
+
+def test_kernel_source_fingerprint_ignores_comments_only():
+    """the fingerprint that ties measured DRAM traffic to the kernel sources
+    is unchanged by comment and blank-line edits and changed by any code
+    edit (including one inside a line that also holds a comment)"""
+    from paper_1904_08684_gb300 import flops as FL
+    base = {n: "" for n in FL.KERNEL_SOURCES}
+    base["dg_tile.cuh"] = 'int a = 1;  // one\n/* block\n comment */\nconst char* s = "// not a comment";\n'
+    h0 = FL.source_hash(lambda n: base[n])
+    cmt = dict(base, **{"dg_tile.cuh": 'int a = 1;  // other words\n\n/* x */\nconst char* s = "// not a comment";\n'})
+    assert FL.source_hash(lambda n: cmt[n]) == h0
+    code = dict(base, **{"dg_tile.cuh": 'int a = 2;  // one\n/* block\n comment */\nconst char* s = "// not a comment";\n'})
+    assert FL.source_hash(lambda n: code[n]) != h0
+    lit = dict(base, **{"dg_tile.cuh": 'int a = 1;  // one\n/* block\n comment */\nconst char* s = "// changed";\n'})
+    assert FL.source_hash(lambda n: lit[n]) != h0
+    py = dict(base, **{"gen_tables.py": "# a comment\n"})
+    assert FL.source_hash(lambda n: py[n]) != h0        # non-C files are hashed verbatim
