@@ -10,8 +10,12 @@ Default workload: ensemble-256, the batched FP32 form of the headline metric:
 256 seeded independent instances (nx, ny uniform in {64..384}, p uniform in
 {1, 2, 3}, periodic, smooth bathymetry of depth 5-20 m, one Gaussian hump
 each, SSP-RK3, per-instance CFL step), FP32 state and contractions with the
-mixed velocity solve (FP32 factors refined once with an FP64 residual), one
-persistent launch per RK stage, each step one CUDA graph.  Beside it, in the
+mixed velocity solve (FP32 factors refined once with a compensated FP32
+residual: the FP64 solution to within FP32 rounding), tile-fused kernels,
+one persistent launch per order class and RK stage, each step one CUDA
+graph.  "e2e" times the same workload from host states to host states
+(dg_batch_step_host: 4.1 GB of FP64 states up and down per step, copies
+overlapped with the compute).  Beside it, in the
 same JSON line, "fp64_plain" holds the plain FP64 path measured on
 waves-p2-512 (512 x 512 quads -> 524,288 triangles, p = 2, periodic, h_b = 10
 + 2 sin(2 pi x) cos(2 pi y), 8 seeded Gaussians, q = 0, SSP-RK3, CFL 0.2), and
