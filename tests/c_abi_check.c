@@ -34,6 +34,16 @@ int main(void) {
   cfg.bc = DG_BC_DIRICHLET; /* needs the manufactured forcing */
   if (dg_init(&cfg, z, z, z, z, NULL, &ctx) != DG_ERR_UNSUPPORTED) fails++;
 
+  /* batch calls: the host-array form validates before any CUDA call */
+  const double* zp[1] = {z};
+  double* outp[1] = {z};
+  dg_batch* b = NULL;
+  cfg.bc = DG_BC_PERIODIC;
+  cfg.p = 4; /* the batched kernels hold p = 1..3 */
+  if (dg_batch_init(1, &cfg, zp, zp, zp, zp, NULL, &b) != DG_ERR_UNSUPPORTED || b != NULL) fails++;
+  if (dg_batch_get_states(NULL, outp, outp, outp) != DG_ERR_ARG) fails++;
+  if (dg_batch_step_host(NULL, zp, zp, zp, outp, outp, outp, NULL) != DG_ERR_ARG) fails++;
+
   printf("%s\n", fails ? "FAIL" : "OK");
   return fails;
 }
