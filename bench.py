@@ -251,6 +251,22 @@ def _dtype(precision, proj):
     return {"fp64": "f32+f64solve", "fp32": "f32", "df64": "f32+df64solve", "mixed": "f32+f64refinedsolve"}[proj]
 
 
+def _single_kernel_form(wl, args):
+    """the kernel form a single context takes (the library's default rule
+    for tile_shape 0: 8 x 8 tiles with the mixed and FP32 solves at p <= 3,
+    8 x 4 tiles with the FP32 solve at p = 4, per-element otherwise)"""
+    names = {1: "8x8", 2: "16x8", 3: "8x4"}
+    if wl.precision != "fp32" or args.tile < 0:
+        return "per-element"
+    if args.tile > 0:
+        return "tile-fused %s quads" % names[args.tile]
+    if wl.p <= 3 and args.proj in ("mixed", "fp32"):
+        return "tile-fused 8x8 quads"
+    if wl.p == 4 and args.proj == "fp32":
+        return "tile-fused 8x4 quads"
+    return "per-element"
+
+
 def _cfg_of(B, wl, args):
     return B.make_config(wl.nx, wl.ny, wl.p, bc=wl.bc, precision=wl.precision, rk_order=wl.rk_order,
                          cfl=wl.cfl, dt=wl.dt, g=wl.g, x0=wl.x0, y0=wl.y0, Lx=wl.Lx, Ly=wl.Ly,
@@ -424,10 +440,7 @@ def run_ours(args, workload=None, proj=None):
            "vs_baseline": None, "dtype": _dtype(wl.precision, args.proj),
            "data": "synthetic (seeded SplitMix64 fields, projected on device)",
            "config": {"workload": wl.name, "elements": wl.E, "p": wl.p, "K": wl.K, "rk_stages": S,
-                      "kernel_form": ("tile-fused %s quads" % {0: "8x8", 1: "8x8", 2: "16x8", 3: "8x4"}[args.tile]
-                                      if wl.precision == "fp32" and (args.tile > 0 or (
-                                          args.tile == 0 and wl.p <= 3 and args.proj in ("mixed", "fp32")))
-                                      else "per-element"),
+                      "kernel_form": _single_kernel_form(wl, args),
                       "dof_per_stage": dof_stage, "precision": wl.precision, "bc": wl.bc,
                       "l2": "working set per stage > L2 (no flush)",
                       "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -126,7 +126,8 @@ typedef struct {
                               intermediates in shared memory; -1 = one thread
                               per triangle with the intermediates in HBM;
                               0 (default) = 8 x 8 tiles at p <= 3 with the
-                              MIXED and FP32 solves, one thread per triangle
+                              MIXED and FP32 solves, 8 x 4 tiles at p = 4
+                              with the FP32 solve, one thread per triangle
                               otherwise (measured faster there).
                               Both give the same scheme (agreeing to FP32
                               rounding); dg_rhs always uses the latter       */

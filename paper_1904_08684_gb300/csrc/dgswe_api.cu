@@ -156,7 +156,9 @@ StageParams<Real> base_params(const dg_ctx* c) {
 }
 
 cudaError_t launch_tile_any(const dg_ctx* c, const StageParams<float>& sp, cudaStream_t s) {
-  const int shape = c->cfg.tile_shape > 1 ? c->cfg.tile_shape - 1 : 0;   // launcher index
+  // launcher index: tile_shape 1..3 -> 0..2; the default (0) takes 8 x 8
+  // tiles, 8 x 4 at p = 4 (its shared memory leaves more resident CTAs)
+  const int shape = c->cfg.tile_shape > 1 ? c->cfg.tile_shape - 1 : (c->cfg.tile_shape == 0 && c->P == 4 ? 2 : 0);
   switch (c->arith) {
     case ARITH_FP32_P64: return tile_fp32p64(c->P, shape, sp, s);
     case ARITH_FP32_PDF: return tile_fp32pdf(c->P, shape, sp, s);
@@ -489,14 +491,15 @@ dg_status create(const dg_config* cfg, const double* d_hb, const double* d_xi, c
   c->arith = arith_of(cfg->precision, cfg->proj_precision);
   c->rsz = c->arith == ARITH_FP64 ? sizeof(double) : sizeof(float);
   // the tile kernel covers FP32 uniform meshes without forcing (periodic or
-  // walls); by default with the mixed and FP32 solves at p <= 3 (at p = 4
-  // its shared memory leaves too few resident warps, and with the FP64 and
-  // double-float solves the halo's extra solves cost more than the traffic
-  // it saves: the per-element kernel measured faster there)
+  // walls); by default with the mixed and FP32 solves at p <= 3, and with
+  // the FP32 solve at p = 4 (1.47x the per-element kernel on 2048^2 quads;
+  // the mixed solve's p = 4 tile kernel spills and measured 1.6x slower than
+  // its per-element kernel, and with the FP64 and double-float solves the
+  // halo's extra solves cost more than the traffic the tiles save)
   const bool light_solve = cfg->proj_precision == DG_PROJ_MIXED || cfg->proj_precision == DG_PROJ_FP32;
+  const bool tile_default = (cfg->p <= 3 && light_solve) || (cfg->p == 4 && cfg->proj_precision == DG_PROJ_FP32);
   c->tiled = c->arith != ARITH_FP64 && !cfg->vertex_xy && cfg->forcing == DG_FORCING_NONE &&
-             cfg->bc != DG_BC_DIRICHLET &&
-             (cfg->tile_shape > 0 || (cfg->tile_shape == 0 && cfg->p <= 3 && light_solve));
+             cfg->bc != DG_BC_DIRICHLET && (cfg->tile_shape > 0 || (cfg->tile_shape == 0 && tile_default));
   c->stream = (cudaStream_t)stream;
   const double hx = cfg->Lx / cfg->nx, hy = cfg->Ly / cfg->ny;
   c->mesh = make_mesh(cfg->nx, cfg->ny, cfg->x0, cfg->y0, cfg->Lx, cfg->Ly, cfg->bc == DG_BC_PERIODIC);

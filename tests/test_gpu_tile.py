@@ -133,10 +133,11 @@ def test_tile_lake_at_rest():
 
 def test_default_kernel_form(oracle_mod):
     """tile_shape 0 takes 8 x 8 tiles with the mixed and FP32 solves at
-    p <= 3 and the per-element kernels otherwise: identical bits to the
-    explicit choice in each case"""
+    p <= 3, 8 x 4 tiles with the FP32 solve at p = 4 and the per-element
+    kernels otherwise: identical bits to the explicit choice in each case"""
     nx, ny, bc = SIZES[0]
-    for p, proj, explicit in ((2, "mixed", 1), (3, "fp32", 1), (2, "fp64", -1), (3, "df64", -1), (4, "mixed", -1)):
+    for p, proj, explicit in ((2, "mixed", 1), (3, "fp32", 1), (2, "fp64", -1), (3, "df64", -1), (4, "mixed", -1),
+                              (4, "fp32", 3)):
         _, fields = _inputs(oracle_mod, nx, ny, p, bc)
         t0, a = _run(nx, ny, p, bc, fields, 8, 0, proj)
         t1, b = _run(nx, ny, p, bc, fields, 8, explicit, proj)
