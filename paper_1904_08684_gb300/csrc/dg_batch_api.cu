@@ -908,20 +908,22 @@ static dg_status ensure_pipeline(dg_batch* b, size_t groups) {
   if (!b->s_down) CK(cudaStreamCreateWithFlags(&b->s_down, cudaStreamNonBlocking));
   for (cudaEvent_t* e : {&b->ev_start, &b->ev_end})
     if (!*e) CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
-  try {
-    while (b->ev_up.size() < groups) {
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      CK(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
-      const cudaError_t ce = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
-      if (ce != cudaSuccess) {
-        cudaEventDestroy(e0);
-        return cuda_status(ce);
-      }
-      b->ev_up.push_back(e0);
-      b->ev_done.push_back(e1);
-    }
+  try {   // reserved first, so that no push_back below can throw
+    b->ev_up.reserve(groups);
+    b->ev_done.reserve(groups);
   } catch (const std::exception&) {
     return DG_ERR_OOM;
+  }
+  while (b->ev_up.size() < groups) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+    const cudaError_t ce = cudaEventCreateWithFlags(&e1, cudaEventDisableTiming);
+    if (ce != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return cuda_status(ce);
+    }
+    b->ev_up.push_back(e0);
+    b->ev_done.push_back(e1);
   }
   // sized once for the largest group count make_groups can give (at most
   // kStepGroups + 3: every class ends one partial group)
@@ -934,6 +936,7 @@ static dg_status step_host_impl(dg_batch* b, const double* const* xi_in, const d
                                 double* const* qy_out, double* t_out) {
   std::vector<StepGroup> gs;
   dg_status s = make_groups(b, gs);
+  if (s == DG_OK && gs.size() > (size_t)(kStepGroups + 3)) s = DG_ERR_ARG;   // cannot happen: see make_groups
   if (s == DG_OK) s = ensure_batch_stage(b, b->stage_total);
   if (s == DG_OK) s = ensure_pipeline(b, gs.size());
   if (s != DG_OK) return s;
